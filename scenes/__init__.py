@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests
+and the benchmark.
+
+This module only draws random numbers and builds camera poses; it holds none
+of the method's arithmetic (no projection, culling, compositing or
+optimiser).  Random numbers come from one counter-based generator, SplitMix64
+(Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014): value i of stream `key` is mix64(key + (i + 1) * GAMMA), so any
+index range can be produced independently of the others.
+
+Parameter rows are float32 [n, 59] in the paper's logical layout (Sec. 2,
+D = 59): mean (3), log-scale (3), quaternion w,x,y,z (4), opacity logit (1),
+SH DC rgb (3), SH rest 15 x rgb (45, coefficient-major, l = 1..3, m = -l..l).
+
+Cameras are dicts with width, height, fx, fy, cx, cy, znear, zfar and R, t of
+the world-to-camera map x_c = R x_w + t (camera looks down +z, y down, x
+right); pixels are sampled at integer coordinates, so the principal point of a
+centred camera is (W/2 - 0.5, H/2 - 0.5).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+D = 59
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        s = np.array([(seed * 0x100000001B3 + stream * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF],
+                     dtype=np.uint64)
+        return _mix64(s)[0]
+
+
+def u64(seed: int, stream: int, start: int, count: int) -> np.ndarray:
+    key = stream_key(seed, stream)
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        return _mix64(key + idx * GAMMA)
+
+
+def uniform(seed: int, stream: int, count: int, lo=0.0, hi=1.0, start: int = 0) -> np.ndarray:
+    """Uniform doubles in [lo, hi): top 53 bits of each draw."""
+    x = (u64(seed, stream, start, count) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * x
+
+
+def normal(seed: int, stream: int, count: int, mean=0.0, std=1.0, start: int = 0) -> np.ndarray:
+    """Box-Muller normals from pairs of uniforms of the same stream."""
+    u = (u64(seed, stream, 2 * start, 2 * count) >> np.uint64(11)).astype(np.float64)
+    u *= 1.0 / 9007199254740992.0
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    return mean + std * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# ----------------------------------------------------------------------------
+# cameras
+# ----------------------------------------------------------------------------
+def look_at(pos, target, up=(0.0, 1.0, 0.0)):
+    """World-to-camera R, t for a camera at `pos` looking at `target`."""
+    pos = np.asarray(pos, np.float64)
+    z = np.asarray(target, np.float64) - pos
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    t = -R @ pos
+    return R, t
+
+
+def pinhole(width, height, fov_x_deg, R, t, znear=0.2, zfar=100.0):
+    fx = (width / 2.0) / math.tan(math.radians(fov_x_deg) / 2.0)
+    return dict(width=int(width), height=int(height), fx=fx, fy=fx,
+                cx=width / 2.0 - 0.5, cy=height / 2.0 - 0.5,
+                znear=float(znear), zfar=float(zfar),
+                R=np.asarray(R, np.float64), t=np.asarray(t, np.float64))
+
+
+def rot_y(deg):
+    a = math.radians(deg)
+    return np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+
+
+# ----------------------------------------------------------------------------
+# Gaussian tables
+# ----------------------------------------------------------------------------
+def _assemble(means, logs, quats, opac, sh):
+    n = means.shape[0]
+    p = np.empty((n, D), np.float32)
+    p[:, 0:3] = means
+    p[:, 3:6] = logs
+    p[:, 6:10] = quats
+    p[:, 10] = opac
+    p[:, 11:59] = sh.reshape(n, 48)
+    return p
+
+
+def random_quats(seed, stream, n):
+    q = normal(seed, stream, 4 * n).reshape(n, 4)
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def cube_scene(n=20000, seed=1000, log_scale_mean=-4.0, log_scale_std=0.5, sh_std=0.2, extent=1.0):
+    """Means uniform in [-extent, extent]^3, log-scales N(mean, std), random unit
+    quaternions, opacity logit N(0, 1), 48 SH coefficients N(0, sh_std)."""
+    means = uniform(seed, 1, 3 * n, -extent, extent).reshape(n, 3)
+    logs = normal(seed, 2, 3 * n, log_scale_mean, log_scale_std).reshape(n, 3)
+    quats = random_quats(seed, 3, n)
+    opac = normal(seed, 4, n)
+    sh = normal(seed, 5, 48 * n, 0.0, sh_std).reshape(n, 16, 3)
+    return _assemble(means, logs, quats, opac, sh)
+
+
+def perturb(params, seed, mean_std=0.02, logscale_std=0.1, opacity_std=0.5, sh_std=0.05):
+    """Training start (or target source): Gaussian noise on means, log-scales,
+    opacity logits and SH coefficients; quaternions are left unchanged."""
+    n = params.shape[0]
+    p = params.astype(np.float64).copy()
+    p[:, 0:3] += normal(seed, 11, 3 * n, 0.0, mean_std).reshape(n, 3)
+    p[:, 3:6] += normal(seed, 12, 3 * n, 0.0, logscale_std).reshape(n, 3)
+    p[:, 10] += normal(seed, 13, n, 0.0, opacity_std)
+    p[:, 11:59] += normal(seed, 14, 48 * n, 0.0, sh_std).reshape(n, 48)
+    return p.astype(np.float32)
+
+
+def small_cube_config(seed=1000, n=20000, size=256):
+    """20,000 Gaussians in [-1,1]^3 (log-scale N(-4, 0.5), opacity logit N(0,1),
+    SH N(0, 0.2)), grouped in 16 blocks of 1,250; a 256x256 camera with a 60
+    degree field of view at distance 3 looking at the origin, and a second
+    camera rotated 20 degrees about the world y axis."""
+    params = cube_scene(n, seed)
+    p1 = np.array([0.0, 0.0, -3.0])
+    R1, t1 = look_at(p1, [0, 0, 0])
+    p2 = rot_y(20.0) @ p1
+    R2, t2 = look_at(p2, [0, 0, 0])
+    cams = [pinhole(size, size, 60.0, R1, t1), pinhole(size, size, 60.0, R2, t2)]
+    return dict(params=params, cams=cams, block_size=(n + 15) // 16)
+
+
+def aerial_block_scene(n=2_000_000, seed=1001, side=1000.0, n_boxes=150, ground_frac=0.8):
+    """Aerial block scene (world z up): a jittered ground grid at z=0 plus box
+    buildings (footprint U[10,40] m, height U[10,80] m) whose walls and roofs
+    carry the remaining Gaussians (area-weighted).  Log-scales log(0.5 *
+    spacing) + N(0, 0.3); SH DC from a smooth colour field, the rest N(0,
+    0.05); opacity logit N(2, 0.5)."""
+    n_ground = int(n * ground_frac)
+    g = int(math.ceil(math.sqrt(n_ground)))
+    spacing = side / g
+    ii = np.arange(n_ground)
+    gx = (ii % g + 0.5) * spacing - side / 2
+    gy = (ii // g + 0.5) * spacing - side / 2
+    jit = uniform(seed, 21, 2 * n_ground, -0.4 * spacing, 0.4 * spacing).reshape(n_ground, 2)
+    ground = np.stack([gx + jit[:, 0], gy + jit[:, 1], np.zeros(n_ground)], 1)
+    nb = n - n_ground
+    # boxes
+    cxy = uniform(seed, 22, 2 * n_boxes, -side / 2 + 40, side / 2 - 40).reshape(n_boxes, 2)
+    fw = uniform(seed, 23, 2 * n_boxes, 10.0, 40.0).reshape(n_boxes, 2)
+    hh = uniform(seed, 24, n_boxes, 10.0, 80.0)
+    # faces: 4 walls + roof, areas
+    areas = np.stack([fw[:, 0] * hh, fw[:, 0] * hh, fw[:, 1] * hh, fw[:, 1] * hh, fw[:, 0] * fw[:, 1]], 1)
+    flat = areas.reshape(-1)
+    cdf = np.cumsum(flat) / flat.sum()
+    pick = np.searchsorted(cdf, uniform(seed, 25, nb), side="right")
+    pick = np.minimum(pick, flat.size - 1)
+    box = pick // 5
+    face = pick % 5
+    a = uniform(seed, 26, nb)
+    b = uniform(seed, 27, nb)
+    wx, wy, h = fw[box, 0], fw[box, 1], hh[box]
+    x0, y0 = cxy[box, 0] - wx / 2, cxy[box, 1] - wy / 2
+    pts = np.empty((nb, 3))
+    # face 0: y = y0 wall, 1: y = y0 + wy, 2: x = x0, 3: x = x0 + wx, 4: roof
+    m = face == 0; pts[m] = np.stack([x0[m] + a[m] * wx[m], y0[m], b[m] * h[m]], 1)
+    m = face == 1; pts[m] = np.stack([x0[m] + a[m] * wx[m], y0[m] + wy[m], b[m] * h[m]], 1)
+    m = face == 2; pts[m] = np.stack([x0[m], y0[m] + a[m] * wy[m], b[m] * h[m]], 1)
+    m = face == 3; pts[m] = np.stack([x0[m] + wx[m], y0[m] + a[m] * wy[m], b[m] * h[m]], 1)
+    m = face == 4; pts[m] = np.stack([x0[m] + a[m] * wx[m], y0[m] + b[m] * wy[m], h[m]], 1)
+    means = np.concatenate([ground, pts], 0)
+    logs = (math.log(0.5 * spacing) + normal(seed, 28, 3 * n, 0.0, 0.3)).reshape(n, 3)
+    quats = random_quats(seed, 29, n)
+    opac = normal(seed, 30, n, 2.0, 0.5)
+    col = np.stack([0.5 + 0.3 * np.sin(means[:, 0] / 37.0 + 0.3 * c) * np.cos(means[:, 1] / 53.0 - 0.7 * c)
+                    + 0.1 * np.sin(means[:, 2] / 11.0 + c) for c in range(3)], 1)
+    sh = normal(seed, 31, 48 * n, 0.0, 0.05).reshape(n, 16, 3)
+    sh[:, 0, :] = (col - 0.5) * 3.5  # smooth DC field, roughly +-1
+    return _assemble(means, logs, quats, opac, sh), spacing
+
+
+def orbit_cameras(n_cams=100, radius=500.0, altitude=150.0, width=1920, height=1080, fov_x=60.0,
+                  znear=0.2, zfar=2000.0, phase=0.0):
+    """Cameras on a circle around the origin at `altitude`, looking at the centre (world z up)."""
+    cams = []
+    for i in range(n_cams):
+        a = phase + 2 * math.pi * i / n_cams
+        pos = [radius * math.cos(a), radius * math.sin(a), altitude]
+        R, t = look_at(pos, [0.0, 0.0, 0.0], up=(0.0, 0.0, 1.0))
+        cams.append(pinhole(width, height, fov_x, R, t, znear, zfar))
+    return cams
+
+
+def aerial_config(n=2_000_000, seed=1001, n_cams=100, width=1920, height=1080, block_size=4096):
+    params, spacing = aerial_block_scene(n, seed)
+    cams = orbit_cameras(n_cams, width=width, height=height)
+    return dict(params=params, cams=cams, block_size=block_size, spacing=spacing)
+
+
+def camera_array(cam) -> np.ndarray:
+    """The oracle's camera layout: W, H, fx, fy, cx, cy, znear, zfar, R (9), t (3)."""
+    return np.concatenate([[cam["width"], cam["height"], cam["fx"], cam["fy"], cam["cx"], cam["cy"],
+                            cam["znear"], cam["zfar"]], np.asarray(cam["R"]).reshape(9),
+                           np.asarray(cam["t"]).reshape(3)]).astype(np.float64)
