@@ -1,0 +1,224 @@
+/*
+ * tidegs.h -- C ABI of the B300 (sm_103a) implementation of the TideGS
+ * out-of-core 3D Gaussian Splatting training step (arXiv 2605.20150).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a tgs_status; TGS_OK is 0.  On failure nothing is
+ *     thrown or aborted across the boundary: the status says what went wrong
+ *     and tgs_last_error() returns a thread-local message.
+ *   - Pointers marked "host" point to CPU memory, "device" to memory of the
+ *     current CUDA device.  Input buffers are borrowed for the duration of the
+ *     call unless stated otherwise; output buffers are owned by the caller.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Device work is ordered after work already
+ *     queued on that stream; results are ready when that stream reaches the
+ *     point after the call.
+ *   - A Gaussian row has D = 59 floats in the paper's logical layout
+ *     (Sec. 2 "Per-Gaussian parameter table", D = 59): mean (3), log-scale (3),
+ *     rotation quaternion w,x,y,z (4), opacity logit (1), SH DC rgb (3), SH rest
+ *     (45 = 15 coefficients x rgb, coefficient-major, l=1..3, m=-l..l).
+ *   - Images are H x W x 3 float32, row-major, pixel (px, py) sampled at its
+ *     integer coordinates.
+ *   - A table is not thread-safe: one calling thread per table.
+ */
+#ifndef TIDEGS_H
+#define TIDEGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TGS_D 59
+#define TGS_TILE 16
+
+typedef int32_t tgs_status;
+enum {
+  TGS_OK = 0,
+  TGS_ERR_INVALID = 1,  /* bad argument (null pointer, size out of range) */
+  TGS_ERR_OOM = 2,      /* device or pinned host allocation failed */
+  TGS_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  TGS_ERR_CAPACITY = 4, /* a working set or buffer exceeds its configured capacity */
+  TGS_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
+  TGS_ERR_STATE = 6     /* call not valid in the table's current state */
+};
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* tgs_last_error(void);
+
+/* Pinhole camera.  A world point x maps to camera coordinates
+ * c = R x + t with world_to_cam = [R | t] (row-major 3x4); the camera looks
+ * down +z, y points down; pixel u = fx c_x / c_z + cx, v = fy c_y / c_z + cy.
+ * znear / zfar bound the visible depth (Sec. 3.3, "6-plane frustum test"). */
+typedef struct tgs_camera {
+  uint32_t width, height;
+  float fx, fy, cx, cy;
+  float znear, zfar;
+  float world_to_cam[12];
+} tgs_camera;
+
+/* Training-table configuration.  Defaults from tgs_default_config(). */
+typedef struct tgs_config {
+  uint32_t block_size;     /* B, Gaussians per block (Sec. 3.3 uses 4096) */
+  uint32_t moments_policy; /* 0: Adam moments stream with their block (persistent);
+                              1: moments dropped on eviction, zeroed on re-admission
+                              (the paper's default "cold restart", Sec. 3.5) */
+  uint32_t prefetch_mode;  /* 0: reactive -- batch t's working set is selected and
+                              streamed at step t (copies exposed);
+                              1: exact next batch (Sec. 3.4-3.5) -- batch t+1's delta is
+                              selected and streamed while batch t computes */
+  uint32_t overlap;        /* 1: copies on dedicated streams overlap compute (Sec. 3.4);
+                              0: copies serialised with compute */
+  uint64_t cache_blocks;   /* C, resident-set capacity in blocks; 0 = all blocks */
+  uint32_t spare_slots;    /* extra HBM slots that receive incoming blocks while the
+                              current step still uses its resident set */
+  uint32_t max_batch;      /* largest camera batch J */
+  uint32_t max_width, max_height;
+  uint32_t quota;          /* per-camera quota of the camera-balanced Top-C;
+                              0xFFFFFFFF = floor(C / (2 J)) */
+  float lambda;            /* residency mix lambda of s(k) (Sec. 3.5) */
+  float lr, beta1, beta2, eps; /* Adam, one learning rate for all 59 columns */
+  float cull_margin_px;    /* Level-1 side-plane margin in pixels */
+  float bg[3];             /* background colour */
+  uint32_t loss;           /* 0: L1 mean, 1: L2 mean (photometric loss f_i, App. A.1) */
+  uint32_t host_bf16;      /* 1: SH-rest coefficients and Adam moments are BF16 in the
+                              host tier and the cache (not the paper's; FP32 = 0) */
+} tgs_config;
+
+void tgs_default_config(tgs_config* cfg);
+
+typedef struct tgs_table tgs_table;
+
+/* Creates a block-virtualised table of n Gaussians (Sec. 3.3, Eq. block_def):
+ * Morton-orders the rows by the codes of their centres, cuts blocks of B rows
+ * (the last block truncated at n), writes the block records to pinned host
+ * memory (the host tier), computes the block bounding spheres and allocates
+ * the HBM working-set cache.
+ * params_host: host, n x 59 row-major, borrowed (copied).
+ * Errors: TGS_ERR_INVALID (n == 0, bad config), TGS_ERR_OOM. */
+tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_host, tgs_table** out);
+
+void tgs_destroy(tgs_table* t);
+
+/* One training step on a camera batch (Sec. 3.2 stages 1-4, Algorithm 1):
+ * culls the batch's blocks, makes its working set resident (streaming only the
+ * delta S+ and writing back dirty evicted blocks S-), renders each camera over
+ * the resident visible blocks, computes the photometric loss against the
+ * targets, back-propagates, applies masked Adam to the touched Gaussians
+ * (App. A.1, Eq. masked_update), marks their blocks dirty and refreshes their
+ * bounds.  With prefetch_mode 1 and next_cams given, it also selects and
+ * starts streaming the next batch's delta while this batch computes.
+ * cams: host, batch cameras (batch <= max_batch).
+ * next_cams: host, the next batch (may be NULL).
+ * targets_dev: device, batch x H x W x 3, or NULL when targets_host is given;
+ *   read after `stream`'s prior work.
+ * targets_host: host (pinned or pageable), used when targets_dev is NULL; copied
+ *   inside the call.
+ * loss_out: host, may be NULL; when given the call waits for the step and writes
+ *   the batch loss (mean over cameras, pixels and channels).
+ * Errors: TGS_ERR_INVALID, TGS_ERR_CAPACITY (a batch's working set exceeds the
+ *   cache), TGS_ERR_CUDA. */
+tgs_status tgs_step(tgs_table* t, const tgs_camera* cams, uint32_t batch, const tgs_camera* next_cams,
+                    uint32_t next_batch, const float* targets_dev, const float* targets_host, void* stream,
+                    float* loss_out);
+
+/* Renders one camera from the current parameters (forward only).  The camera's
+ * working set is made resident first (it counts as a step of the residency
+ * policy, without parameter updates).  image_dev: device, H x W x 3. */
+tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, void* stream);
+
+/* Waits for all queued work of the table. */
+tgs_status tgs_sync(tgs_table* t);
+
+/* Flushes dirty resident blocks to the host tier (a consistency barrier,
+ * Sec. 3.4) and writes the parameters in the caller's original row order.
+ * out_host: host, n x 59. */
+tgs_status tgs_get_params(tgs_table* t, float* out_host);
+
+/* Same barrier; writes the state in block (Morton) order: params, first and
+ * second Adam moments (each n x 59, any may be NULL), and the per-block Adam
+ * step counters (K values, may be NULL). */
+tgs_status tgs_get_state(tgs_table* t, float* params_host, float* m1_host, float* m2_host, uint32_t* steps_host);
+
+/* perm_host[g] = original row of the Gaussian with block-order id g (n values). */
+tgs_status tgs_get_block_order(tgs_table* t, int64_t* perm_host);
+
+/* Block bounding spheres (cx, cy, cz, r), K x 4, as the next cull uses them. */
+tgs_status tgs_get_spheres(tgs_table* t, float* spheres_host);
+
+/* Sizes: n Gaussians, K blocks, number of HBM slots. */
+tgs_status tgs_get_sizes(tgs_table* t, uint64_t* n, uint64_t* k, uint64_t* slots);
+
+/* Set state of the last step, as K-byte arrays (1 = member): the visible set
+ * K_t of the computed batch, the resident set R_t it rendered from, and the
+ * per-camera visible sets (batch x K); s_plus / s_minus receive the block ids
+ * streamed in / evicted to make R_t resident (ascending) with their counts.
+ * Any pointer may be NULL. */
+tgs_status tgs_get_sets(tgs_table* t, uint8_t* k_visible, uint8_t* r_resident, uint8_t* k_per_camera,
+                        int64_t* s_plus, uint64_t* n_plus, int64_t* s_minus, uint64_t* n_minus);
+
+/* Per-camera intermediates of the last step (camera index j of the batch), in
+ * render-list order (ascending Gaussian id over the blocks of R_t & K_t):
+ *   ids (int64 Gaussian ids), splat (float x 12: u, v, depth, A, B, C, opacity,
+ *   r, g, b, radius, visible), rect (int32 x 4: x0, y0, x1, y1);
+ *   pair_vals (uint32 render-list positions of the sorted pairs),
+ *   ranges (uint32 x 2 per tile); image (H x W x 3), t_final (H x W),
+ *   n_last (int32, H x W); grad2d (float x 9 per Gaussian: u, v, A, B, C,
+ *   opacity, r, g, b).  Call with all array pointers NULL to get the counts. */
+tgs_status tgs_get_camera_record(tgs_table* t, uint32_t j, uint64_t* n_gauss, uint64_t* n_pairs,
+                                 int64_t* ids, float* splat, int32_t* rect, uint32_t* pair_vals,
+                                 uint32_t* ranges, float* image, float* t_final, int32_t* n_last,
+                                 float* grad2d);
+
+/* Counters (Tab. 4/5/9 style). */
+typedef struct tgs_stats {
+  uint64_t steps;
+  uint64_t bytes_h2d, bytes_d2h;
+  uint64_t blocks_in, blocks_out, writebacks, readmissions, cold_restarts;
+  uint64_t kernel_launches;
+  double stall_ms;
+  uint64_t last_pairs, last_visible, last_render_blocks;
+} tgs_stats;
+tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
+
+/* ---------------------------------------------------------------------------
+ * Resident (fully in-HBM) rasteriser for autograd frameworks: the standard
+ * 3DGS forward/backward that Sec. 3.3 "Level 2" runs on the resident blocks.
+ * Parameters live in caller-owned device memory in block layout
+ * [ceil(n/B)][59][B] float (field-major inside a block); Gaussian id g is
+ * block g / B, lane g % B; lanes past n are ignored.
+ * ------------------------------------------------------------------------- */
+typedef struct tgs_raster tgs_raster;
+
+/* max_gaussians: largest n; max_width / max_height: largest image. */
+tgs_status tgs_raster_create(uint64_t max_gaussians, uint32_t max_width, uint32_t max_height, tgs_raster** out);
+void tgs_raster_destroy(tgs_raster* r);
+
+/* Forward render of one camera over all n Gaussians of params_dev.
+ * image_dev: device, H x W x 3.  The context keeps what the backward needs
+ * for this one camera until the next forward. */
+tgs_status tgs_raster_forward(tgs_raster* r, const float* params_dev, uint64_t n, uint32_t block_size,
+                              const tgs_camera* cam, const float* bg3, float* image_dev, void* stream);
+
+/* Backward of the last forward (same params, camera and background):
+ * dl_dimage_dev (device, H x W x 3) -> grad_dev (device, params layout,
+ * ACCUMULATED with +=).  touched_dev (device, n bytes, may be NULL) is set to 1
+ * for Gaussians with a non-empty tile rect. */
+tgs_status tgs_raster_backward(tgs_raster* r, const float* params_dev, uint64_t n, uint32_t block_size,
+                               const tgs_camera* cam, const float* bg3, const float* dl_dimage_dev,
+                               float* grad_dev, uint8_t* touched_dev, void* stream);
+
+/* Masked Adam (App. A.1, Eq. masked_update) on block-layout device arrays:
+ * rows with touched[g] != 0 update m, v and params; step_dev holds per-block
+ * step counters (ceil(n/B) uint32), incremented for blocks with a touched row
+ * before their rows use them for bias correction. */
+tgs_status tgs_adam(float* params_dev, const float* grad_dev, float* m1_dev, float* m2_dev,
+                    const uint8_t* touched_dev, uint32_t* step_dev, uint64_t n, uint32_t block_size, float lr,
+                    float beta1, float beta2, float eps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TIDEGS_H */

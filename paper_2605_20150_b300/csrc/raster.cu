@@ -1,0 +1,921 @@
+// Level-2 rendering kernels (Sec. 3.3 "Level 2"): the standard 3DGS
+// forward/backward run over the Gaussians of a render list of resident
+// blocks, written for sm_103a.
+//
+//  k_preprocess      one thread per Gaussian: coalesced field-major loads from
+//                    the block slot, EWA projection, degree-3 SH colour, tile
+//                    rect; exact FP32 key path for centre and depth.
+//  visible compaction + stable depth sort of the visible Gaussians + pair
+//  emission in depth order + stable tile sort (the tile/depth order of the
+//  pairs equals a stable sort of (tile << 32 | depth bits) keys emitted in id
+//  order, with far fewer radix passes over the pairs).
+//  k_raster_fwd      one CTA per 16x16 tile, batches of 256 splats staged in
+//                    shared memory, front-to-back blending with the 0.99 clamp,
+//                    the 1/255 skip and the T < 1e-4 stop.
+//  k_raster_bwd      reverse traversal from each pixel's last contributor,
+//                    recomputing T_i = T_{i+1} / (1 - alpha_i); per-Gaussian
+//                    2D gradients are reduced across the warp with shuffles and
+//                    added with one atomic per (warp, Gaussian, field).
+//  k_preprocess_bwd  chain rule to the 59 parameters.
+//  k_adam            masked Adam (App. A.1, Eq. masked_update).
+#include <math.h>
+
+#include "raster.cuh"
+#include "sort.cuh"
+
+namespace tgs {
+
+namespace {
+
+constexpr int PP_THREADS = 256;
+
+// Real SH normalisations (sqrt(2) Re/Im of the Condon-Shortley complex
+// harmonics, l <= 3), from their closed forms:
+constexpr float K00 = 0.28209479177387814f;  // 1/(2 sqrt(pi))
+constexpr float K1 = 0.4886025119029199f;    // sqrt(3/(4 pi))
+constexpr float K2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float K2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float K2c = 0.5462742152960396f;   // sqrt(15/pi)/4
+constexpr float K3a = 0.5900435899266435f;   // sqrt(35/(2 pi))/4
+constexpr float K3b = 2.890611442640554f;    // sqrt(105/pi)/2
+constexpr float K3c = 0.4570457994644658f;   // sqrt(21/(2 pi))/4
+constexpr float K3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+constexpr float K3e = 1.445305721320277f;    // sqrt(105/pi)/4
+
+// Basis values Y[16] at unit direction (x, y, z), ordered l, m = -l..l.
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float Y[16]) {
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = K00;
+  Y[1] = -K1 * y;
+  Y[2] = K1 * z;
+  Y[3] = -K1 * x;
+  Y[4] = K2a * x * y;
+  Y[5] = -K2a * y * z;
+  Y[6] = K2b * (2.f * zz - xx - yy);
+  Y[7] = -K2a * x * z;
+  Y[8] = K2c * (xx - yy);
+  Y[9] = -K3a * y * (3.f * xx - yy);
+  Y[10] = K3b * x * y * z;
+  Y[11] = -K3c * y * (4.f * zz - xx - yy);
+  Y[12] = K3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -K3c * x * (4.f * zz - xx - yy);
+  Y[14] = K3e * z * (xx - yy);
+  Y[15] = -K3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of the basis w.r.t. the (unnormalised-polynomial) direction.
+__device__ __forceinline__ void sh_grad(float x, float y, float z, float G[16][3]) {
+  float xx = x * x, yy = y * y, zz = z * z;
+  G[0][0] = 0; G[0][1] = 0; G[0][2] = 0;
+  G[1][0] = 0; G[1][1] = -K1; G[1][2] = 0;
+  G[2][0] = 0; G[2][1] = 0; G[2][2] = K1;
+  G[3][0] = -K1; G[3][1] = 0; G[3][2] = 0;
+  G[4][0] = K2a * y; G[4][1] = K2a * x; G[4][2] = 0;
+  G[5][0] = 0; G[5][1] = -K2a * z; G[5][2] = -K2a * y;
+  G[6][0] = -2.f * K2b * x; G[6][1] = -2.f * K2b * y; G[6][2] = 4.f * K2b * z;
+  G[7][0] = -K2a * z; G[7][1] = 0; G[7][2] = -K2a * x;
+  G[8][0] = 2.f * K2c * x; G[8][1] = -2.f * K2c * y; G[8][2] = 0;
+  G[9][0] = -K3a * 6.f * x * y; G[9][1] = -K3a * (3.f * xx - 3.f * yy); G[9][2] = 0;
+  G[10][0] = K3b * y * z; G[10][1] = K3b * x * z; G[10][2] = K3b * x * y;
+  G[11][0] = K3c * 2.f * x * y; G[11][1] = -K3c * (4.f * zz - xx - 3.f * yy); G[11][2] = -K3c * 8.f * y * z;
+  G[12][0] = -K3d * 6.f * x * z; G[12][1] = -K3d * 6.f * y * z; G[12][2] = K3d * (6.f * zz - 3.f * xx - 3.f * yy);
+  G[13][0] = -K3c * (4.f * zz - 3.f * xx - yy); G[13][1] = K3c * 2.f * x * y; G[13][2] = -K3c * 8.f * x * z;
+  G[14][0] = K3e * 2.f * x * z; G[14][1] = -K3e * 2.f * y * z; G[14][2] = K3e * (xx - yy);
+  G[15][0] = -K3a * (3.f * xx - 3.f * yy); G[15][1] = K3a * 6.f * x * y; G[15][2] = 0;
+}
+
+// Rotation matrix of the normalised quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[3][3]) {
+  R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
+  R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+  R[2][0] = 2.f * (x * z - w * y); R[2][1] = 2.f * (y * z + w * x); R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+struct Geo {
+  float Rq[3][3], sc[3], qn, qw, qx, qy, qz;
+  float S[6];          // Sigma: xx xy xz yy yz zz
+  float T[2][3];       // J Rc
+  float a, b, c, det;  // dilated 2D covariance
+  bool clx, cly;
+  float xc, yc;        // clamped tx/tz, ty/tz
+};
+
+// Projection geometry shared by the forward and the backward preprocess.
+__device__ __forceinline__ void geometry(const DevCam& c, const float* p, uint32_t B, const KeyPath& k, Geo& g) {
+  g.sc[0] = expf(p[3 * B]);
+  g.sc[1] = expf(p[4 * B]);
+  g.sc[2] = expf(p[5 * B]);
+  float qw = p[6 * B], qx = p[7 * B], qy = p[8 * B], qz = p[9 * B];
+  g.qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  float inv = 1.f / g.qn;
+  g.qw = qw * inv; g.qx = qx * inv; g.qy = qy * inv; g.qz = qz * inv;
+  quat_rot(g.qw, g.qx, g.qy, g.qz, g.Rq);
+  float M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[a][b] = g.Rq[a][b] * g.sc[b];
+  g.S[0] = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2];
+  g.S[1] = M[0][0] * M[1][0] + M[0][1] * M[1][1] + M[0][2] * M[1][2];
+  g.S[2] = M[0][0] * M[2][0] + M[0][1] * M[2][1] + M[0][2] * M[2][2];
+  g.S[3] = M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2];
+  g.S[4] = M[1][0] * M[2][0] + M[1][1] * M[2][1] + M[1][2] * M[2][2];
+  g.S[5] = M[2][0] * M[2][0] + M[2][1] * M[2][1] + M[2][2] * M[2][2];
+  float tz = k.tz;
+  float xr = k.tx / tz, yr = k.ty / tz;
+  g.clx = xr < -c.limx || xr > c.limx;
+  g.cly = yr < -c.limy || yr > c.limy;
+  g.xc = fminf(fmaxf(xr, -c.limx), c.limx);
+  g.yc = fminf(fmaxf(yr, -c.limy), c.limy);
+  float J00 = c.fx / tz, J02 = -c.fx * g.xc / tz;
+  float J11 = c.fy / tz, J12 = -c.fy * g.yc / tz;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    g.T[0][j] = J00 * c.R[0 + j] + J02 * c.R[6 + j];
+    g.T[1][j] = J11 * c.R[3 + j] + J12 * c.R[6 + j];
+  }
+  float TS[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    TS[a][0] = g.T[a][0] * g.S[0] + g.T[a][1] * g.S[1] + g.T[a][2] * g.S[2];
+    TS[a][1] = g.T[a][0] * g.S[1] + g.T[a][1] * g.S[3] + g.T[a][2] * g.S[4];
+    TS[a][2] = g.T[a][0] * g.S[2] + g.T[a][1] * g.S[4] + g.T[a][2] * g.S[5];
+  }
+  g.a = TS[0][0] * g.T[0][0] + TS[0][1] * g.T[0][1] + TS[0][2] * g.T[0][2] + DILATION;
+  g.b = TS[0][0] * g.T[1][0] + TS[0][1] * g.T[1][1] + TS[0][2] * g.T[1][2];
+  g.c = TS[1][0] * g.T[1][0] + TS[1][1] * g.T[1][1] + TS[1][2] * g.T[1][2] + DILATION;
+  g.det = g.a * g.c - g.b * g.b;
+}
+
+struct PPOut {
+  float2* xy;
+  float* depth;
+  float4* conic_o;
+  float4* rgb;
+  ushort4* rect;
+  int* radius;
+  uint32_t* ntiles;
+  uint32_t* vflag;
+};
+
+__global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam c, PPOut o, uint8_t* touched,
+                                                          uint32_t* item_touched, unsigned cpi) {
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  const uint32_t B = rl.B;
+  if (lane >= B) return;
+  const uint64_t i = (uint64_t)item * B + lane;
+  uint32_t area = 0;
+  if (lane < rl.item_count[item]) {
+    const float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+    float mx = p[0], my = p[B], mz = p[2 * B];
+    KeyPath k = key_path(c, mx, my, mz);
+    if (k.tz > c.znear && k.tz <= c.zfar) {
+      Geo g;
+      geometry(c, p, B, k, g);
+      if (g.det > 0.f) {
+        float mid = 0.5f * (g.a + g.c);
+        float lam1 = mid + sqrtf(fmaxf(0.1f, mid * mid - g.det));
+        int r = (int)ceilf(3.f * sqrtf(lam1));
+        int x0 = min(max(floor_div_tile(k.u, -r), 0), c.TX);
+        int x1 = min(max(floor_div_tile(k.u, r) + 1, 0), c.TX);
+        int y0 = min(max(floor_div_tile(k.v, -r), 0), c.TY);
+        int y1 = min(max(floor_div_tile(k.v, r) + 1, 0), c.TY);
+        if (x1 > x0 && y1 > y0) {
+          area = (uint32_t)((x1 - x0) * (y1 - y0));
+          // colour from the degree-3 SH at the view direction
+          float dx = mx - c.campos[0], dy = my - c.campos[1], dz = mz - c.campos[2];
+          float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+          float Y[16];
+          sh_eval(dx * il, dy * il, dz * il, Y);
+          float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) col[ch] += Y[kk] * p[(uint64_t)(11 + 3 * kk + ch) * B];
+          uint32_t clampbits = (col[0] < 0.f ? 1u : 0u) | (col[1] < 0.f ? 2u : 0u) | (col[2] < 0.f ? 4u : 0u);
+          float opac = 1.f / (1.f + expf(-p[10 * B]));
+          o.xy[i] = make_float2(k.u, k.v);
+          o.depth[i] = k.tz;
+          o.conic_o[i] = make_float4(g.c / g.det, -g.b / g.det, g.a / g.det, opac);
+          o.rgb[i] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f),
+                                 __uint_as_float(clampbits));
+          o.rect[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+          o.radius[i] = r;
+          if (touched) touched[i] = 1;
+          if (item_touched) item_touched[item] = 1;
+        }
+      }
+    }
+  }
+  o.ntiles[i] = area;
+  o.vflag[i] = area ? 1u : 0u;
+}
+
+__global__ void k_compact_visible(uint64_t V, const uint32_t* __restrict__ ntiles, const uint32_t* __restrict__ pos,
+                                  const float* __restrict__ depth, uint32_t* __restrict__ dkeys,
+                                  uint32_t* __restrict__ dvals) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V || ntiles[i] == 0) return;
+  uint32_t q = pos[i];
+  dkeys[q] = __float_as_uint(depth[i]);  // depth > 0: the bits order like the values
+  dvals[q] = (uint32_t)i;
+}
+
+__global__ void k_gather_counts(uint64_t nv, const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ ntiles,
+                                uint32_t* __restrict__ cnt) {
+  uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nv) cnt[s] = ntiles[dvals[s]];
+}
+
+__global__ void k_emit_pairs(uint64_t nv, const uint32_t* __restrict__ dvals, const ushort4* __restrict__ rect,
+                             const uint32_t* __restrict__ off, int TX, uint32_t* __restrict__ pkeys,
+                             uint32_t* __restrict__ pvals) {
+  uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nv) return;
+  uint32_t i = dvals[s];
+  ushort4 r = rect[i];
+  uint32_t o = off[s];
+  for (int ty = r.y; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.z; ++tx) {
+      pkeys[o] = (uint32_t)(ty * TX + tx);
+      pvals[o] = i;
+      ++o;
+    }
+}
+
+__global__ void k_ranges(uint64_t np, const uint32_t* __restrict__ pkeys, uint2* __restrict__ ranges) {
+  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  uint32_t t = pkeys[p];
+  if (p == 0 || pkeys[p - 1] != t) ranges[t].x = (uint32_t)p;
+  if (p == np - 1 || pkeys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+}
+
+__global__ void __launch_bounds__(TILE_PIX) k_raster_fwd(const uint2* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ pvals,
+                                                        const float2* __restrict__ xy,
+                                                        const float4* __restrict__ conic_o,
+                                                        const float4* __restrict__ rgb, int W, int H, int TX,
+                                                        float3 bg, float* __restrict__ img,
+                                                        float* __restrict__ t_final, int* __restrict__ n_last) {
+  __shared__ float2 s_xy[TILE_PIX];
+  __shared__ float4 s_co[TILE_PIX];
+  __shared__ float4 s_rgb[TILE_PIX];
+  const int tile = blockIdx.x;
+  const int px = (tile % TX) * TILE + (threadIdx.x & 15);
+  const int py = (tile / TX) * TILE + (threadIdx.x >> 4);
+  const bool inside = px < W && py < H;
+  const uint2 r = ranges[tile];
+  const int n = (int)(r.y - r.x);
+  const float fpx = (float)px, fpy = (float)py;
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int last = 0;
+  bool done = !inside;
+  for (int b = 0; b < n; b += TILE_PIX) {
+    if (__syncthreads_count(done) == TILE_PIX) break;
+    int k = b + threadIdx.x;
+    if (k < n) {
+      uint32_t id = pvals[r.x + k];
+      s_xy[threadIdx.x] = xy[id];
+      s_co[threadIdx.x] = conic_o[id];
+      s_rgb[threadIdx.x] = rgb[id];
+    }
+    __syncthreads();
+    const int m = min(TILE_PIX, n - b);
+    for (int j = 0; !done && j < m; ++j) {
+      float2 g = s_xy[j];
+      float4 co = s_co[j];
+      float dx, dy;
+      float power = splat_power(fpx, fpy, g.x, g.y, co.x, co.y, co.z, dx, dy);
+      if (power > 0.f) continue;
+      float G;
+      float alpha = splat_alpha(co.w, power, G);
+      if (alpha < ALPHA_MIN) continue;
+      float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+      if (Tn < T_STOP) {
+        done = true;
+        break;
+      }
+      float4 cc = s_rgb[j];
+      float w = alpha * T;
+      C0 += cc.x * w;
+      C1 += cc.y * w;
+      C2 += cc.z * w;
+      T = Tn;
+      last = b + j + 1;
+    }
+  }
+  if (inside) {
+    uint64_t pix = (uint64_t)py * W + px;
+    img[3 * pix + 0] = C0 + T * bg.x;
+    img[3 * pix + 1] = C1 + T * bg.y;
+    img[3 * pix + 2] = C2 + T * bg.z;
+    t_final[pix] = T;
+    n_last[pix] = last;
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(TILE_PIX) k_raster_bwd(const uint2* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ pvals,
+                                                        const float2* __restrict__ xy,
+                                                        const float4* __restrict__ conic_o,
+                                                        const float4* __restrict__ rgb, int W, int H, int TX,
+                                                        float3 bg, const float* __restrict__ t_final,
+                                                        const int* __restrict__ n_last,
+                                                        const float* __restrict__ dl_dimg, float* __restrict__ g2,
+                                                        uint64_t V) {
+  __shared__ uint32_t s_id[TILE_PIX];
+  __shared__ float2 s_xy[TILE_PIX];
+  __shared__ float4 s_co[TILE_PIX];
+  __shared__ float4 s_rgb[TILE_PIX];
+  __shared__ int s_max;
+  const int tile = blockIdx.x;
+  const int px = (tile % TX) * TILE + (threadIdx.x & 15);
+  const int py = (tile / TX) * TILE + (threadIdx.x >> 4);
+  const bool inside = px < W && py < H;
+  const uint2 r = ranges[tile];
+  const uint64_t pix = (uint64_t)py * W + px;
+  float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
+  int last = 0;
+  if (inside) {
+    T = t_final[pix];
+    last = n_last[pix];
+    gr = dl_dimg[3 * pix + 0];
+    gg = dl_dimg[3 * pix + 1];
+    gb = dl_dimg[3 * pix + 2];
+  }
+  const float Tf = T;
+  const float bgdot = bg.x * gr + bg.y * gg + bg.z * gb;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  if (last > 0) atomicMax(&s_max, last);
+  __syncthreads();
+  const int maxlast = s_max;
+  const float fpx = (float)px, fpy = (float)py;
+  for (int b = maxlast; b > 0; b -= TILE_PIX) {
+    __syncthreads();
+    int k = b - 1 - (int)threadIdx.x;
+    if (k >= 0) {
+      uint32_t id = pvals[r.x + k];
+      s_id[threadIdx.x] = id;
+      s_xy[threadIdx.x] = xy[id];
+      s_co[threadIdx.x] = conic_o[id];
+      s_rgb[threadIdx.x] = rgb[id];
+    }
+    __syncthreads();
+    const int m = min(TILE_PIX, b);
+    for (int j = 0; j < m; ++j) {
+      const int pos = b - 1 - j;
+      float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool contrib = false;
+      if (pos < last) {
+        float2 g = s_xy[j];
+        float4 co = s_co[j];
+        float dx, dy;
+        float power = splat_power(fpx, fpy, g.x, g.y, co.x, co.y, co.z, dx, dy);
+        float G;
+        float alpha = splat_alpha(co.w, power, G);
+        if (power <= 0.f && alpha >= ALPHA_MIN) {
+          contrib = true;
+          float oma = __fsub_rn(1.f, alpha);
+          float Ti = __fdiv_rn(T, oma);
+          float4 cc = s_rgb[j];
+          float w = alpha * Ti;
+          v[6] = w * gr;
+          v[7] = w * gg;
+          v[8] = w * gb;
+          float dal = Ti * (gr * (cc.x - S0) + gg * (cc.y - S1) + gb * (cc.z - S2)) - Tf * bgdot / oma;
+          S0 = alpha * cc.x + oma * S0;
+          S1 = alpha * cc.y + oma * S1;
+          S2 = alpha * cc.z + oma * S2;
+          T = Ti;
+          if (__fmul_rn(co.w, G) <= ALPHA_MAX) {
+            v[5] = G * dal;
+            float dpw = alpha * dal;
+            v[0] = dpw * (co.x * dx + co.y * dy);
+            v[1] = dpw * (co.y * dx + co.z * dy);
+            v[2] = -0.5f * dpw * dx * dx;
+            v[3] = -dpw * dx * dy;
+            v[4] = -0.5f * dpw * dy * dy;
+          }
+        }
+      }
+      if (__ballot_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] = warp_sum(v[q]);
+        if ((threadIdx.x & 31) == 0) {
+          uint32_t id = s_id[j];
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            if (v[q] != 0.f) atomicAdd(&g2[(uint64_t)q * V + id], v[q]);
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
+                                                              const uint32_t* __restrict__ ntiles,
+                                                              const float4* __restrict__ rgbv,
+                                                              const float4* __restrict__ conic_o,
+                                                              const float* __restrict__ g2, uint64_t V,
+                                                              float* __restrict__ grad, int grad_pool,
+                                                              unsigned cpi) {
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  const uint32_t B = rl.B;
+  if (lane >= B) return;
+  const uint64_t i = (uint64_t)item * B + lane;
+  if (lane >= rl.item_count[item] || ntiles[i] == 0) return;
+  const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+  const float* p = rl.base + sbase;
+  float* out = grad_pool ? grad + sbase : grad + i;
+  const uint64_t ostride = grad_pool ? B : V;
+  const float gu = g2[i], gv = g2[V + i], gA = g2[2 * V + i], gB = g2[3 * V + i], gC = g2[4 * V + i];
+  const float gop = g2[5 * V + i];
+  const float gcol[3] = {g2[6 * V + i], g2[7 * V + i], g2[8 * V + i]};
+  const float mx = p[0], my = p[B], mz = p[2 * B];
+  float dmu[3] = {0.f, 0.f, 0.f};
+  // ---- colour ----
+  {
+    float dx = mx - c.campos[0], dy = my - c.campos[1], dz = mz - c.campos[2];
+    float len = sqrtf(dx * dx + dy * dy + dz * dz);
+    float il = 1.f / len;
+    float d[3] = {dx * il, dy * il, dz * il};
+    float Y[16];
+    sh_eval(d[0], d[1], d[2], Y);
+    float Gs[16][3];
+    sh_grad(d[0], d[1], d[2], Gs);
+    uint32_t cl = __float_as_uint(rgbv[i].w);
+    float gc[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) gc[ch] = (cl >> ch) & 1u ? 0.f : gcol[ch];
+    float dd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        uint64_t f = 11 + 3 * kk + ch;
+        out[f * ostride] += Y[kk] * gc[ch];
+        float shv = p[f * B];
+        float w = gc[ch] * shv;
+        dd[0] += w * Gs[kk][0];
+        dd[1] += w * Gs[kk][1];
+        dd[2] += w * Gs[kk][2];
+      }
+    }
+    float dot = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dmu[a] += (dd[a] - d[a] * dot) * il;
+  }
+  // ---- opacity ----
+  {
+    float op = conic_o[i].w;
+    out[10 * ostride] += gop * op * (1.f - op);
+  }
+  // ---- geometry ----
+  KeyPath k = key_path(c, mx, my, mz);
+  Geo g;
+  geometry(c, p, B, k, g);
+  const float tz = k.tz;
+  const float idet = 1.f / g.det;
+  const float id2 = idet * idet;
+  const float dla = (-g.c * g.c * gA + g.b * g.c * gB - g.b * g.b * gC) * id2;
+  const float dlc = (-g.b * g.b * gA + g.a * g.b * gB - g.a * g.a * gC) * id2;
+  const float dlb = (2.f * g.b * g.c * gA - (g.a * g.c + g.b * g.b) * gB + 2.f * g.a * g.b * gC) * id2;
+  const float Gc[2][2] = {{dla, 0.5f * dlb}, {0.5f * dlb, dlc}};
+  float GT[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) GT[a][b] = Gc[a][0] * g.T[0][b] + Gc[a][1] * g.T[1][b];
+  // dL/dSigma = T^T Gc T (symmetric)
+  float dS[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dS[a][b] = g.T[0][a] * GT[0][b] + g.T[1][a] * GT[1][b];
+  const float Sg[3][3] = {{g.S[0], g.S[1], g.S[2]}, {g.S[1], g.S[3], g.S[4]}, {g.S[2], g.S[4], g.S[5]}};
+  // dL/dT = 2 Gc T Sigma, dL/dJ = dL/dT Rc^T
+  float dT[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dT[a][b] = 2.f * (GT[a][0] * Sg[0][b] + GT[a][1] * Sg[1][b] + GT[a][2] * Sg[2][b]);
+  float dJ00 = dT[0][0] * c.R[0] + dT[0][1] * c.R[1] + dT[0][2] * c.R[2];
+  float dJ02 = dT[0][0] * c.R[6] + dT[0][1] * c.R[7] + dT[0][2] * c.R[8];
+  float dJ11 = dT[1][0] * c.R[3] + dT[1][1] * c.R[4] + dT[1][2] * c.R[5];
+  float dJ12 = dT[1][0] * c.R[6] + dT[1][1] * c.R[7] + dT[1][2] * c.R[8];
+  float tz2 = tz * tz, tz3 = tz2 * tz;
+  float dt[3] = {0.f, 0.f, 0.f};
+  dt[2] += -c.fx / tz2 * dJ00 - c.fy / tz2 * dJ11;
+  if (!g.clx) {
+    dt[0] += -c.fx / tz2 * dJ02;
+    dt[2] += 2.f * c.fx * k.tx / tz3 * dJ02;
+  } else {
+    dt[2] += c.fx * g.xc / tz2 * dJ02;
+  }
+  if (!g.cly) {
+    dt[1] += -c.fy / tz2 * dJ12;
+    dt[2] += 2.f * c.fy * k.ty / tz3 * dJ12;
+  } else {
+    dt[2] += c.fy * g.yc / tz2 * dJ12;
+  }
+  dt[0] += gu * c.fx / tz;
+  dt[1] += gv * c.fy / tz;
+  dt[2] += -gu * c.fx * k.tx / tz2 - gv * c.fy * k.ty / tz2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dmu[a] += c.R[a] * dt[0] + c.R[3 + a] * dt[1] + c.R[6 + a] * dt[2];
+  out[0] += dmu[0];
+  out[ostride] += dmu[1];
+  out[2 * ostride] += dmu[2];
+  // Sigma = M M^T, M = Rq diag(sc)
+  float M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[a][b] = g.Rq[a][b] * g.sc[b];
+  float dR[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float dsb = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float dM = 2.f * (dS[a][0] * M[0][b] + dS[a][1] * M[1][b] + dS[a][2] * M[2][b]);
+      dsb += dM * g.Rq[a][b];
+      dR[a][b] = dM * g.sc[b];
+    }
+    out[(3 + b) * ostride] += dsb * g.sc[b];
+  }
+  const float w = g.qw, x = g.qx, y = g.qy, z = g.qz;
+  float gw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+  float gx = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                    z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+  float gy = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                    w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+  float gz = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                    y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+  float qd = gw * w + gx * x + gy * y + gz * z;
+  float iq = 1.f / g.qn;
+  out[6 * ostride] += (gw - w * qd) * iq;
+  out[7 * ostride] += (gx - x * qd) * iq;
+  out[8 * ostride] += (gy - y * qd) * iq;
+  out[9 * ostride] += (gz - z * qd) * iq;
+}
+
+__global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
+                                                    const uint8_t* __restrict__ touched,
+                                                    const uint32_t* __restrict__ block_step, uint64_t V, float lr,
+                                                    float b1, float b2, float eps, unsigned cpi) {
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  const uint32_t B = rl.B;
+  if (lane >= B) return;
+  const uint64_t i = (uint64_t)item * B + lane;
+  if (lane >= rl.item_count[item] || !touched[i]) return;
+  const float tau = (float)block_step[rl.item_block[item]];
+  const float c1 = 1.f - powf(b1, tau), c2 = 1.f - powf(b2, tau);
+  const float ic1 = 1.f / c1, ic2 = 1.f / c2;
+  float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+  float* m = p + rl.m_off;
+  float* v = p + rl.v_off;
+#pragma unroll 4
+  for (int f = 0; f < D; ++f) {
+    const uint64_t o = (uint64_t)f * B;
+    float gf = grad[(uint64_t)f * V + i];
+    float mf = b1 * m[o] + (1.f - b1) * gf;
+    float vf = b2 * v[o] + (1.f - b2) * gf * gf;
+    m[o] = mf;
+    v[o] = vf;
+    p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+  }
+}
+
+__global__ void k_mark_touched(RenderList rl, const uint32_t* __restrict__ item_touched, uint32_t* block_step,
+                               uint8_t* dirty) {
+  unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= rl.n_items || !item_touched[j]) return;
+  block_step[rl.item_block[j]] += 1;
+  if (dirty) dirty[rl.item_slot[j]] = 1;
+}
+
+__device__ __forceinline__ float block_reduce(float v, float* sm, bool is_max, bool is_min) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, u) : (is_min ? fminf(v, u) : v + u);
+  }
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  float r = sm[0];
+  for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = is_max ? fmaxf(r, sm[k]) : (is_min ? fminf(r, sm[k]) : r + sm[k]);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_bounds(RenderList rl, const uint32_t* __restrict__ only,
+                                               float4* __restrict__ spheres) {
+  __shared__ float sm[8];
+  const unsigned item = blockIdx.x;
+  if (only && !only[item]) return;
+  const uint32_t B = rl.B, cnt = rl.item_count[item];
+  const float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float v = p[(uint64_t)a * B + l];
+      mn[a] = fminf(mn[a], v);
+      mx[a] = fmaxf(mx[a], v);
+    }
+  float c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float lo = block_reduce(mn[a], sm, false, true);
+    float hi = block_reduce(mx[a], sm, true, false);
+    c[a] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+  }
+  float r = 0.f;
+  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
+    float dx = p[l] - c[0], dy = p[(uint64_t)B + l] - c[1], dz = p[(uint64_t)2 * B + l] - c[2];
+    float ls = fmaxf(fmaxf(p[(uint64_t)3 * B + l], p[(uint64_t)4 * B + l]), p[(uint64_t)5 * B + l]);
+    r = fmaxf(r, sqrtf(dx * dx + dy * dy + dz * dz) + 3.f * expf(ls));
+  }
+  r = block_reduce(r, sm, true, false);
+  if (threadIdx.x == 0) spheres[rl.item_block[item]] = make_float4(c[0], c[1], c[2], r);
+}
+
+__global__ void k_loss(const float* __restrict__ img, const float* __restrict__ tgt, uint64_t n, int kind,
+                       float* __restrict__ grad, float* __restrict__ loss_sum) {
+  __shared__ float sm[8];
+  float acc = 0.f;
+  const float inv = 1.f / (float)n;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    float d = img[i] - tgt[i];
+    if (kind == 0) {
+      acc += fabsf(d);
+      grad[i] = (d > 0.f ? inv : (d < 0.f ? -inv : 0.f));
+    } else {
+      acc += d * d;
+      grad[i] = 2.f * d * inv;
+    }
+  }
+  float s = block_reduce(acc, sm, false, false);
+  if (threadIdx.x == 0) atomicAdd(loss_sum, s);
+}
+
+__global__ void k_mark_visible(RenderList rl, const uint32_t* __restrict__ ntiles, uint8_t* __restrict__ touched,
+                               unsigned cpi) {
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  if (lane >= rl.B || lane >= rl.item_count[item]) return;
+  const uint64_t i = (uint64_t)item * rl.B + lane;
+  if (ntiles[i]) touched[(uint64_t)rl.item_block[item] * rl.B + lane] = 1;
+}
+
+__global__ void k_dense_steps(const uint8_t* __restrict__ touched, uint64_t n, uint32_t B, uint32_t* step) {
+  const uint64_t k = blockIdx.x;
+  int any = 0;
+  for (uint32_t l = threadIdx.x; l < B; l += blockDim.x) {
+    uint64_t g = k * B + l;
+    if (g < n && touched[g]) any = 1;
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0) step[k] += 1;
+}
+
+__global__ void k_adam_dense(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m,
+                             float* __restrict__ v, const uint8_t* __restrict__ touched,
+                             const uint32_t* __restrict__ step, uint64_t n, uint32_t B, float lr, float b1, float b2,
+                             float eps) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n || !touched[g]) return;
+  const uint64_t k = g / B, l = g % B;
+  const float tau = (float)step[k];
+  const float ic1 = 1.f / (1.f - powf(b1, tau)), ic2 = 1.f / (1.f - powf(b2, tau));
+  const uint64_t base = k * (uint64_t)D * B + l;
+#pragma unroll 4
+  for (int f = 0; f < D; ++f) {
+    const uint64_t o = base + (uint64_t)f * B;
+    float gf = gr[o];
+    float mf = b1 * m[o] + (1.f - b1) * gf;
+    float vf = b2 * v[o] + (1.f - b2) * gf * gf;
+    m[o] = mf;
+    v[o] = vf;
+    p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+  }
+}
+
+}  // namespace
+
+void mark_visible_bytes(const RenderList& rl, const CamState& cs, uint8_t* touched, cudaStream_t s) {
+  if (rl.capacity() == 0) return;
+  unsigned cpi = div_up(rl.B, PP_THREADS);
+  k_mark_visible<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cs.ntiles, touched, cpi);
+  TGS_LAUNCHED();
+}
+
+void adam_dense(float* params, const float* grad, float* m1, float* m2, const uint8_t* touched, uint32_t* step,
+                uint64_t n, uint32_t B, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  uint64_t K = (n + B - 1) / B;
+  k_dense_steps<<<(unsigned)K, 256, 0, s>>>(touched, n, B, step);
+  TGS_LAUNCHED();
+  k_adam_dense<<<div_up(n, 256), 256, 0, s>>>(params, grad, m1, m2, touched, step, n, B, lr, b1, b2, eps);
+  TGS_LAUNCHED();
+}
+
+DevCam make_devcam(const tgs_camera& c) {
+  DevCam d;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) d.R[3 * a + b] = c.world_to_cam[4 * a + b];
+    d.t[a] = c.world_to_cam[4 * a + 3];
+  }
+  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy; d.znear = c.znear; d.zfar = c.zfar;
+  for (int j = 0; j < 3; ++j) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) s += (double)c.world_to_cam[4 * a + j] * (double)c.world_to_cam[4 * a + 3];
+    d.campos[j] = (float)(-s);
+  }
+  d.W = (int)c.width;
+  d.H = (int)c.height;
+  d.limx = (float)(1.3 * (double)c.width / (2.0 * (double)c.fx));
+  d.limy = (float)(1.3 * (double)c.height / (2.0 * (double)c.fy));
+  d.TX = (d.W + TILE - 1) / TILE;
+  d.TY = (d.H + TILE - 1) / TILE;
+  return d;
+}
+
+void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h) {
+  cs.cap_v = cap_v;
+  cs.cap_pix = (uint64_t)max_w * max_h;
+  cs.cap_tiles = (uint64_t)((max_w + TILE - 1) / TILE) * ((max_h + TILE - 1) / TILE);
+  uint64_t V = cap_v > 0 ? cap_v : 1;
+  TGS_CUDA(cudaMalloc(&cs.xy, V * sizeof(float2)));
+  TGS_CUDA(cudaMalloc(&cs.depth, V * sizeof(float)));
+  TGS_CUDA(cudaMalloc(&cs.conic_o, V * sizeof(float4)));
+  TGS_CUDA(cudaMalloc(&cs.rgb, V * sizeof(float4)));
+  TGS_CUDA(cudaMalloc(&cs.rect, V * sizeof(ushort4)));
+  TGS_CUDA(cudaMalloc(&cs.radius, V * sizeof(int)));
+  TGS_CUDA(cudaMalloc(&cs.ntiles, V * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.scan, V * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.dkeys, 2 * V * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.dvals, 2 * V * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.g2, 9 * V * sizeof(float)));
+  TGS_CUDA(cudaMalloc(&cs.ranges, cs.cap_tiles * sizeof(uint2)));
+  TGS_CUDA(cudaMalloc(&cs.t_final, cs.cap_pix * sizeof(float)));
+  TGS_CUDA(cudaMalloc(&cs.n_last, cs.cap_pix * sizeof(int)));
+  TGS_CUDA(cudaMalloc(&cs.counters, 4 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&cs.counters_host, 4 * sizeof(uint32_t)));
+  cs.cap_pairs = 0;
+  cam_state_grow_pairs(cs, cap_pairs > 0 ? cap_pairs : 1024, 0);
+}
+
+void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
+  uint64_t want = need > cs.cap_v ? need : cs.cap_v;
+  if (need <= cs.cap_pairs && cs.scratch) return;
+  if (need > cs.cap_pairs) {
+    if (s) TGS_CUDA(cudaStreamSynchronize(s));
+    if (cs.pkeys) TGS_CUDA(cudaFree(cs.pkeys));
+    if (cs.pvals) TGS_CUDA(cudaFree(cs.pvals));
+    uint64_t cap = need + need / 4 + 1024;
+    TGS_CUDA(cudaMalloc(&cs.pkeys, 2 * cap * sizeof(uint32_t)));
+    TGS_CUDA(cudaMalloc(&cs.pvals, 2 * cap * sizeof(uint32_t)));
+    cs.cap_pairs = cap;
+    want = cap > cs.cap_v ? cap : cs.cap_v;
+  }
+  size_t sb = radix_scratch_bytes(want);
+  size_t sc = scan_scratch_bytes(want);
+  if (sc > sb) sb = sc;
+  if (sb > cs.scratch_bytes) {
+    if (s) TGS_CUDA(cudaStreamSynchronize(s));
+    if (cs.scratch) TGS_CUDA(cudaFree(cs.scratch));
+    TGS_CUDA(cudaMalloc(&cs.scratch, sb));
+    cs.scratch_bytes = sb;
+  }
+}
+
+void cam_state_free(CamState& cs) {
+  void* ptrs[] = {cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.dkeys,
+                  cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (cs.counters_host) cudaFreeHost(cs.counters_host);
+  cs = CamState();
+}
+
+static int bits_for(uint64_t n) {
+  int b = 1;
+  while ((1ull << b) < n) ++b;
+  return b;
+}
+
+void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
+                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s) {
+  const uint64_t V = rl.capacity();
+  TGS_CHECK(V <= cs.cap_v, TGS_ERR_CAPACITY, "render list exceeds the per-camera capacity");
+  TGS_CHECK((uint64_t)cam.W * cam.H <= cs.cap_pix && (uint64_t)cam.TX * cam.TY <= cs.cap_tiles, TGS_ERR_CAPACITY,
+            "image larger than the configured maximum");
+  cs.W = cam.W; cs.H = cam.H; cs.TX = cam.TX; cs.TY = cam.TY;
+  const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
+  const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
+  cs.n_vis = 0;
+  cs.n_pairs = 0;
+  TGS_CUDA(cudaMemsetAsync(cs.ranges, 0, tiles * sizeof(uint2), s));
+  if (V > 0) {
+    unsigned cpi = div_up(rl.B, PP_THREADS);
+    PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
+    k_preprocess<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
+    TGS_LAUNCHED();
+    exclusive_scan_u32(cs.scan, cs.scan, cs.counters, V, cs.scratch, s);
+    k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
+    TGS_LAUNCHED();
+    TGS_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TGS_CUDA(cudaStreamSynchronize(s));
+    cs.n_vis = cs.counters_host[0];
+  }
+  const uint64_t nv = cs.n_vis;
+  if (nv > 0) {
+    radix_sort_pairs(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv, 32, cs.scratch, s);
+    k_gather_counts<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.ntiles, cs.scan);
+    TGS_LAUNCHED();
+    exclusive_scan_u32(cs.scan, cs.scan, cs.counters + 1, nv, cs.scratch, s);
+    TGS_CUDA(cudaMemcpyAsync(cs.counters_host + 1, cs.counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TGS_CUDA(cudaStreamSynchronize(s));
+    cs.n_pairs = cs.counters_host[1];
+    cam_state_grow_pairs(cs, cs.n_pairs, s);
+    const uint64_t np = cs.n_pairs;
+    if (np > 0) {
+      k_emit_pairs<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys, cs.pvals);
+      TGS_LAUNCHED();
+      radix_sort_pairs(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np,
+                       bits_for(tiles), cs.scratch, s);
+      k_ranges<<<div_up(np, 256), 256, 0, s>>>(np, cs.pkeys, cs.ranges);
+      TGS_LAUNCHED();
+    }
+  }
+  k_raster_fwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+                                                   cam.TX, bg3, image, cs.t_final, cs.n_last);
+  TGS_LAUNCHED();
+}
+
+void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,
+                        const float* dl_dimage, cudaStream_t s) {
+  const uint64_t V = rl.capacity();
+  const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
+  if (V == 0) return;
+  TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * cs.cap_v * sizeof(float), s));
+  if (cs.n_pairs == 0) return;
+  const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
+  k_raster_bwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.cap_v);
+  TGS_LAUNCHED();
+}
+
+void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad,
+                            bool grad_pool, cudaStream_t s) {
+  if (rl.capacity() == 0 || cs.n_vis == 0) return;
+  unsigned cpi = div_up(rl.B, PP_THREADS);
+  k_preprocess_bwd<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v,
+                                                          grad, grad_pool ? 1 : 0, cpi);
+  TGS_LAUNCHED();
+}
+
+void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const uint32_t* block_step,
+                      float lr, float b1, float b2, float eps, cudaStream_t s) {
+  if (rl.capacity() == 0) return;
+  unsigned cpi = div_up(rl.B, PP_THREADS);
+  k_adam<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2, eps, cpi);
+  TGS_LAUNCHED();
+}
+
+void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
+                         cudaStream_t s) {
+  if (rl.n_items == 0) return;
+  k_mark_touched<<<div_up(rl.n_items, 256), 256, 0, s>>>(rl, item_touched, block_step, dirty);
+  TGS_LAUNCHED();
+}
+
+void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s) {
+  if (rl.n_items == 0) return;
+  k_bounds<<<rl.n_items, 256, 0, s>>>(rl, only_flag, spheres);
+  TGS_LAUNCHED();
+}
+
+void photometric_loss(const float* img, const float* target, uint64_t n, int kind, float* grad, float* loss_sum,
+                      cudaStream_t s) {
+  if (n == 0) return;
+  unsigned grid = div_up(n, 256);
+  if (grid > 4 * NSM) grid = 4 * NSM;
+  k_loss<<<grid, 256, 0, s>>>(img, target, n, kind, grad, loss_sum);
+  TGS_LAUNCHED();
+}
+
+}  // namespace tgs

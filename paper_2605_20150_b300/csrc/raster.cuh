@@ -1,0 +1,110 @@
+// Level-2 rendering (Sec. 3.3 "Level 2"): the standard 3DGS projection,
+// tile binning, depth sort, front-to-back compositing and their backward,
+// run over the Gaussians of a render list of resident blocks.
+#pragma once
+#include "common.cuh"
+
+namespace tgs {
+
+// Gaussians addressed through a list of resident blocks.  Block j of the list
+// lives in slot item_slot[j] of a pool whose slots are `slot_stride` floats
+// apart; inside a slot, field f of lane l is at f * B + l (params), and at
+// m_off + f * B + l / v_off + f * B + l for the Adam moments when present.
+// Render-list position of lane l of item j: j * B + l.
+struct RenderList {
+  float* base;
+  uint64_t slot_stride;
+  uint32_t B;
+  uint32_t n_items;
+  const uint32_t* item_slot;   // device [n_items]
+  const uint32_t* item_count;  // device [n_items], Gaussians in the block
+  const uint32_t* item_block;  // device [n_items], block id
+  uint64_t m_off, v_off;       // moment offsets inside a slot (floats)
+  uint64_t capacity() const { return (uint64_t)n_items * B; }
+};
+
+// Per-camera state of one render (capacities fixed at allocation).
+struct CamState {
+  uint64_t cap_v = 0, cap_pairs = 0, cap_pix = 0, cap_tiles = 0;
+  // per render-list position
+  float2* xy = nullptr;
+  float* depth = nullptr;
+  float4* conic_o = nullptr;   // A, B, C, opacity
+  float4* rgb = nullptr;       // r, g, b, clamp bits (as float)
+  ushort4* rect = nullptr;     // x0, y0, x1, y1 (tiles)
+  int* radius = nullptr;
+  uint32_t* ntiles = nullptr;
+  uint32_t* scan = nullptr;    // V: visibility scan, then pair offsets
+  uint32_t* dkeys = nullptr;   // V x 2 (ping-pong): depth keys / positions
+  uint32_t* dvals = nullptr;
+  float* g2 = nullptr;         // 9 x V: dL/d(u, v, A, B, C, opacity, r, g, b)
+  // per pair
+  uint32_t* pkeys = nullptr;   // 2 x cap_pairs (ping-pong)
+  uint32_t* pvals = nullptr;
+  // per tile / pixel
+  uint2* ranges = nullptr;
+  float* t_final = nullptr;
+  int* n_last = nullptr;
+  // scratch for scans and sorts
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  uint32_t* counters = nullptr;  // device [4]: n_vis, n_pairs
+  uint32_t* counters_host = nullptr;  // pinned mirror
+  // results of the last render
+  uint64_t n_vis = 0, n_pairs = 0;
+  int W = 0, H = 0, TX = 0, TY = 0;
+};
+
+void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h);
+void cam_state_free(CamState& cs);
+void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
+
+// Forward: preprocess -> visible compaction -> depth sort -> pair emission ->
+// tile sort -> ranges -> compositing.  touched (render-list bytes, may be
+// null) gets 1 for visible Gaussians; item_touched (per item, may be null)
+// gets 1 for items with a visible Gaussian.  Synchronises the stream twice
+// to read the visible and pair counts.
+void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
+                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s);
+
+// Backward of the compositing into cs.g2 (zeroed here).
+void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,
+                        const float* dl_dimage, cudaStream_t s);
+
+// Chain rule from cs.g2 to the 59 parameters.  Accumulates (+=) into
+// `grad`: either a local array [59][cap_v] (grad_pool == false) or a pool with
+// the render list's slot layout (grad_pool == true, grad = pool base).
+void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad,
+                            bool grad_pool, cudaStream_t s);
+
+// Masked Adam over the render list: rows with touched != 0 update params and
+// moments in the pool; `grad` is the local [59][cap_v] array; step counters per
+// block id (already incremented for this step).
+void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const uint32_t* block_step,
+                      float lr, float b1, float b2, float eps, cudaStream_t s);
+
+// Per-item bookkeeping before Adam: for items with item_touched != 0,
+// block_step[block] += 1 and dirty[slot] = 1.
+void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
+                         cudaStream_t s);
+
+// touched[j * B + l] |= (Gaussian l of item j had a non-empty tile rect in cs).
+void mark_visible_bytes(const RenderList& rl, const CamState& cs, uint8_t* touched, cudaStream_t s);
+
+// Masked Adam on block-layout arrays [ceil(n/B)][59][B]: per-block step
+// counters are incremented for blocks with a touched row, then touched rows
+// update m, v and params.
+void adam_dense(float* params, const float* grad, float* m1, float* m2, const uint8_t* touched, uint32_t* step,
+                uint64_t n, uint32_t B, float lr, float b1, float b2, float eps, cudaStream_t s);
+
+// Bounding spheres (Sec. 3.3 "Level 1") of the listed blocks: centre = middle
+// of the means' box, radius = max(|mu - c| + 3 max exp(log-scale)); written to
+// spheres[block].  only_flag (per item, may be null) restricts to flagged items.
+void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s);
+
+// Photometric loss over n values: writes dL/dimage and accumulates the sum of
+// per-value losses into *loss_sum (device float, zeroed by the caller).
+void photometric_loss(const float* img, const float* target, uint64_t n, int kind, float* grad, float* loss_sum,
+                      cudaStream_t s);
+
+}  // namespace tgs

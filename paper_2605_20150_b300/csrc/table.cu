@@ -1,0 +1,506 @@
+// Block-virtualised training table (Sec. 3.2-3.5): the pinned host tier, the
+// HBM working-set cache of block slots, the copy streams and the step.
+//
+// Streams: `ctl` runs Level-1 culling and Algorithm 1, `h2d` streams S+ into
+// slots, `d2h` writes dirty S- blocks back, `comp` renders and trains.  With
+// the exact next-batch prefetch, batch t+1's delta is selected at the start
+// of step t and its incoming blocks are copied into spare slots while batch t
+// computes (Sec. 3.4 "Hierarchical asynchronous execution"); blocks that can
+// only go into slots freed by S- are copied after that write-back.
+#include <algorithm>
+#include <cstring>
+#include <thread>
+
+#include "sort.cuh"
+#include "table.cuh"
+
+namespace tgs {
+
+namespace {
+
+template <class T>
+void dalloc(T*& p, uint64_t count) {
+  TGS_CUDA(cudaMalloc((void**)&p, (count > 0 ? count : 1) * sizeof(T)));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace
+
+RenderList Table::render_list(uint32_t n_items) const {
+  RenderList rl;
+  rl.base = pool;
+  rl.slot_stride = rec_floats;
+  rl.B = B;
+  rl.n_items = n_items;
+  rl.item_slot = rl_dev;
+  rl.item_count = rl_dev + max_items;
+  rl.item_block = rl_dev + 2 * (uint64_t)max_items;
+  rl.m_off = (uint64_t)D * B;
+  rl.v_off = 2ull * D * B;
+  return rl;
+}
+
+void Table::create(const tgs_config& c, uint64_t n, const float* params) {
+  cfg = c;
+  TGS_CHECK(n > 0 && params, TGS_ERR_INVALID, "tgs_create: n must be > 0 and params non-null");
+  TGS_CHECK(c.block_size >= 1 && c.block_size <= 65536, TGS_ERR_INVALID, "block_size out of range [1, 65536]");
+  TGS_CHECK(c.max_batch >= 1 && c.max_width >= 1 && c.max_height >= 1, TGS_ERR_INVALID, "bad batch/image limits");
+  TGS_CHECK(n < (1ull << 32), TGS_ERR_INVALID, "n must be below 2^32");
+  TGS_CHECK(c.host_bf16 == 0, TGS_ERR_INVALID, "host_bf16 is not available in this build");
+  N = n;
+  B = c.block_size;
+  K = (N + B - 1) / B;
+  words = (K + 31) / 32;
+  C = c.cache_blocks == 0 || c.cache_blocks > K ? K : c.cache_blocks;
+  n_slots = C + (C < K ? c.spare_slots : 0);
+  if (n_slots > K) n_slots = K;
+  rec_floats = 3ull * D * B;
+  max_items = (uint32_t)C;
+  V_cap = (uint64_t)max_items * B;
+
+  TGS_CUDA(cudaStreamCreateWithFlags(&comp, cudaStreamNonBlocking));
+  TGS_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
+  TGS_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
+  TGS_CUDA(cudaStreamCreateWithFlags(&ctl, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user})
+    TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  TGS_CUDA(cudaEventCreate(&ev_stall_a));
+  TGS_CUDA(cudaEventCreate(&ev_stall_b));
+
+  // ---- Morton order on the device (Sec. 3.3): centres -> codes -> stable sort
+  {
+    float* means = nullptr;
+    uint32_t *codes = nullptr, *pm = nullptr;
+    void* scr = nullptr;
+    float* aabb = nullptr;
+    dalloc(means, 3 * N);
+    dalloc(codes, 2 * N);
+    dalloc(pm, 2 * N);
+    TGS_CUDA(cudaMalloc(&scr, radix_scratch_bytes(N)));
+    dalloc(aabb, 16);
+    TGS_CUDA(cudaMemcpy2DAsync(means, 3 * sizeof(float), params, D * sizeof(float), 3 * sizeof(float), N,
+                               cudaMemcpyHostToDevice, comp));
+    morton_order(means, N, pm, codes, codes + N, pm + N, scr, aabb, comp);
+    perm.resize(N);
+    TGS_CUDA(cudaMemcpyAsync(perm.data(), pm, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, comp));
+    TGS_CUDA(cudaStreamSynchronize(comp));
+    dfree(means); dfree(codes); dfree(pm); dfree(scr); dfree(aabb);
+  }
+
+  // ---- host tier: K block records [params | m | v], field-major inside
+  TGS_CUDA(cudaHostAlloc((void**)&host, K * rec_floats * sizeof(float), cudaHostAllocPortable));
+  {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nt; ++w)
+      th.emplace_back([&, w]() {
+        for (uint64_t k = w; k < K; k += nt) {
+          float* rec = host + k * rec_floats;
+          std::memset(rec + (uint64_t)D * B, 0, 2ull * D * B * sizeof(float));
+          for (uint32_t l = 0; l < B; ++l) {
+            uint64_t g = k * B + l;
+            if (g >= N) {
+              for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = 0.f;
+              continue;
+            }
+            const float* row = params + (uint64_t)perm[g] * D;
+            for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = row[f];
+          }
+        }
+      });
+    for (auto& t : th) t.join();
+  }
+
+  // ---- device cache and state
+  dalloc(pool, n_slots * rec_floats);
+  dalloc(spheres, K);
+  dalloc(ages, K);
+  dalloc(block_step, K);
+  dalloc(dirty_dev, n_slots);
+  TGS_CUDA(cudaMemsetAsync(ages, 0, K * sizeof(uint32_t), comp));
+  {
+    // never-accessed blocks start with the oldest age
+    std::vector<uint32_t> a(K, 126u);
+    TGS_CUDA(cudaMemcpy(ages, a.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  }
+  TGS_CUDA(cudaMemsetAsync(block_step, 0, K * sizeof(uint32_t), comp));
+  TGS_CUDA(cudaMemsetAsync(dirty_dev, 0, n_slots, comp));
+  for (uint32_t** b : {&r_bits, &r_next_bits, &acc_bits, &acc_next_bits, &kvis_union}) {
+    dalloc(*b, words);
+    TGS_CUDA(cudaMemsetAsync(*b, 0, words * sizeof(uint32_t), comp));
+  }
+  dalloc(kvis, (uint64_t)cfg.max_batch * words);
+  dalloc(planes_dev, cfg.max_batch);
+  TGS_CUDA(cudaMallocHost(&planes_host, cfg.max_batch * sizeof(Planes)));
+  dalloc(rb.flag, K);
+  dalloc(rb.pos, K);
+  dalloc(rb.key, 2 * K);
+  dalloc(rb.blk, 2 * K);
+  dalloc(rb.sel, K);
+  dalloc(rb.tmp, K);
+  dalloc(rb.tmp2, K);
+  dalloc(rb.counters, 16);
+  TGS_CUDA(cudaMalloc(&rb.scratch, residency_scratch_bytes(K)));
+  dalloc(lists_dev, 3 * K + 16);
+  TGS_CUDA(cudaMallocHost(&lists_host, (3 * K + 16) * sizeof(uint32_t)));
+  dalloc(rl_dev, 3ull * max_items);
+  TGS_CUDA(cudaMallocHost(&rl_host, 3ull * max_items * sizeof(uint32_t)));
+  const uint64_t pix = (uint64_t)cfg.max_width * cfg.max_height;
+  cams.resize(cfg.max_batch);
+  for (auto& cs : cams) cam_state_alloc(cs, V_cap, 4 * V_cap, (int)cfg.max_width, (int)cfg.max_height);
+  dalloc(images, cfg.max_batch * pix * 3);
+  dalloc(dl_dimg, cfg.max_batch * pix * 3);
+  dalloc(targets_buf, cfg.max_batch * pix * 3);
+  dalloc(touched, V_cap);
+  dalloc(item_touched, max_items);
+  dalloc(grad_local, (uint64_t)D * V_cap);
+  dalloc(loss_dev, 4);
+  TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
+
+  // ---- initial bounding spheres: stream the means and log-scales of every
+  // block through the first slots of the pool
+  {
+    uint64_t chunk = std::min<uint64_t>(n_slots, max_items);
+    for (uint64_t k0 = 0; k0 < K; k0 += chunk) {
+      uint64_t m = std::min(chunk, K - k0);
+      TGS_CUDA(cudaMemcpy2DAsync(pool, rec_floats * sizeof(float), host + k0 * rec_floats,
+                                 rec_floats * sizeof(float), 6ull * B * sizeof(float), m,
+                                 cudaMemcpyHostToDevice, comp));
+      for (uint64_t j = 0; j < m; ++j) {
+        uint64_t blk = k0 + j;
+        rl_host[j] = (uint32_t)j;
+        rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - blk * B);
+        rl_host[2ull * max_items + j] = (uint32_t)blk;
+      }
+      TGS_CUDA(cudaMemcpyAsync(rl_dev, rl_host, 3ull * max_items * sizeof(uint32_t), cudaMemcpyHostToDevice, comp));
+      block_bounds(render_list((uint32_t)m), nullptr, spheres, comp);
+      TGS_CUDA(cudaStreamSynchronize(comp));
+    }
+  }
+  slot_of.assign(K, -1);
+  block_of_slot.assign(n_slots, -1);
+  dirty_host.assign(n_slots, 0);
+  slot_free_ev.assign(n_slots, nullptr);
+  slot_has_ev.assign(n_slots, 0);
+  for (auto& e : slot_free_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  TGS_CUDA(cudaEventRecord(ev_comp, comp));
+  TGS_CUDA(cudaDeviceSynchronize());
+}
+
+void Table::destroy() {
+  if (comp) cudaStreamSynchronize(comp);
+  if (h2d) cudaStreamSynchronize(h2d);
+  if (d2h) cudaStreamSynchronize(d2h);
+  if (ctl) cudaStreamSynchronize(ctl);
+  for (auto& cs : cams) cam_state_free(cs);
+  void* dev[] = {pool, spheres, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
+                 kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
+                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, grad_local,
+                 loss_dev};
+  for (void* p : dev) dfree(p);
+  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host};
+  for (void* p : hst)
+    if (p) cudaFreeHost(p);
+  for (auto& e : slot_free_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b})
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : {comp, h2d, d2h, ctl})
+    if (s) cudaStreamDestroy(s);
+}
+
+// Stage 1 + Algorithm 1 for a batch: cull, select R_next, derive S+ / S- and
+// the render list, assign slots.  Host waits for the (small) lists.
+void Table::prepare(const tgs_camera* cs, uint32_t J, Prepared& out) {
+  TGS_CHECK(J >= 1 && J <= cfg.max_batch, TGS_ERR_INVALID, "batch size out of range");
+  for (uint32_t j = 0; j < J; ++j) {
+    TGS_CHECK(cs[j].width == cs[0].width && cs[j].height == cs[0].height, TGS_ERR_INVALID,
+              "cameras of a batch must share the image size");
+    TGS_CHECK(cs[j].width <= cfg.max_width && cs[j].height <= cfg.max_height, TGS_ERR_INVALID,
+              "camera larger than max_width x max_height");
+    TGS_CHECK(cs[j].znear > 0.f && cs[j].zfar > cs[j].znear && cs[j].fx > 0.f && cs[j].fy > 0.f,
+              TGS_ERR_INVALID, "bad camera intrinsics");
+    planes_host[j] = frustum_planes(cs[j], cfg.cull_margin_px);
+  }
+  out = Prepared();
+  out.cams.assign(cs, cs + J);
+  // spheres reflect every step already enqueued on the compute stream
+  TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+  TGS_CUDA(cudaMemcpyAsync(planes_dev, planes_host, J * sizeof(Planes), cudaMemcpyHostToDevice, ctl));
+  cull_blocks(spheres, K, planes_dev, (int)J, kvis, kvis_union, ctl);
+  uint64_t quota = cfg.quota == 0xFFFFFFFFu ? C / (2 * J) : cfg.quota;
+  if (quota * J > C) quota = C / J;
+  residency(acc_bits, r_bits, kvis, kvis_union, (int)J, K, ages, C, cfg.lambda, quota, r_next_bits,
+            lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl);
+  TGS_CUDA(cudaMemcpyAsync(lists_host, rb.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaStreamSynchronize(ctl));
+  const uint32_t np = lists_host[0], nm = lists_host[1], nr = lists_host[2];
+  uint32_t cnts[3] = {np, nm, nr};
+  std::vector<uint32_t>* dst[3] = {&out.s_plus, &out.s_minus, &out.render_blocks};
+  for (int q = 0; q < 3; ++q) {
+    if (cnts[q])
+      TGS_CUDA(cudaMemcpyAsync(lists_host, lists_dev + (uint64_t)q * K, cnts[q] * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, ctl));
+    TGS_CUDA(cudaStreamSynchronize(ctl));
+    dst[q]->assign(lists_host, lists_host + cnts[q]);
+  }
+  // the selected set becomes the current one for the next selection
+  std::swap(r_bits, r_next_bits);
+  std::swap(acc_bits, acc_next_bits);
+  // per-camera visible sets of this batch (debug getters)
+  last_kvis_host.resize((uint64_t)J * words);
+  last_r_host.resize(words);
+  TGS_CUDA(cudaMemcpyAsync(last_kvis_host.data(), kvis, (uint64_t)J * words * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaMemcpyAsync(last_r_host.data(), r_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaStreamSynchronize(ctl));
+  out.kvis_host = last_kvis_host;
+  out.r_host = last_r_host;
+
+  // ---- slot assignment: free slots (ascending) for S+ in ascending id order,
+  // the rest into the slots that S- frees (ascending)
+  CopyPlan& pl = out.plan;
+  std::vector<uint32_t> free_slots;
+  for (uint64_t s = 0; s < n_slots; ++s)
+    if (block_of_slot[s] < 0) free_slots.push_back((uint32_t)s);
+  std::vector<uint32_t> ev_slots;
+  for (uint32_t b : out.s_minus) {
+    TGS_CHECK(slot_of[b] >= 0, TGS_ERR_STATE, "evicted block is not resident");
+    ev_slots.push_back((uint32_t)slot_of[b]);
+    pl.evict_block.push_back(b);
+    pl.evict_slot.push_back((uint32_t)slot_of[b]);
+  }
+  std::sort(ev_slots.begin(), ev_slots.end());
+  size_t fi = 0, ei = 0;
+  for (uint32_t b : out.s_plus) {
+    if (fi < free_slots.size()) {
+      pl.early_block.push_back(b);
+      pl.early_slot.push_back(free_slots[fi++]);
+    } else {
+      TGS_CHECK(ei < ev_slots.size(), TGS_ERR_CAPACITY, "no slot left for an incoming block");
+      pl.late_block.push_back(b);
+      pl.late_slot.push_back(ev_slots[ei++]);
+    }
+  }
+  // host mirrors describe the state after this selection's copies
+  for (size_t i = 0; i < pl.evict_block.size(); ++i) {
+    slot_of[pl.evict_block[i]] = -1;
+    block_of_slot[pl.evict_slot[i]] = -1;
+  }
+  for (size_t i = 0; i < pl.early_block.size(); ++i) {
+    slot_of[pl.early_block[i]] = pl.early_slot[i];
+    block_of_slot[pl.early_slot[i]] = pl.early_block[i];
+  }
+  for (size_t i = 0; i < pl.late_block.size(); ++i) {
+    slot_of[pl.late_block[i]] = pl.late_slot[i];
+    block_of_slot[pl.late_slot[i]] = pl.late_block[i];
+  }
+  out.valid = true;
+}
+
+static void copy_block_in(Table& t, uint32_t b, uint32_t s, cudaStream_t st) {
+  const uint64_t pf = (uint64_t)D * t.B;
+  float* dst = t.pool + (uint64_t)s * t.rec_floats;
+  const float* src = t.host + (uint64_t)b * t.rec_floats;
+  if (t.slot_has_ev[s]) TGS_CUDA(cudaStreamWaitEvent(st, t.slot_free_ev[s], 0));
+  if (t.cfg.moments_policy == 1) {
+    TGS_CUDA(cudaMemcpyAsync(dst, src, pf * sizeof(float), cudaMemcpyHostToDevice, st));
+    TGS_CUDA(cudaMemsetAsync(dst + pf, 0, 2 * pf * sizeof(float), st));
+    TGS_CUDA(cudaMemsetAsync(t.block_step + b, 0, sizeof(uint32_t), st));
+    t.stats.bytes_h2d += pf * sizeof(float);
+    t.stats.cold_restarts++;
+  } else {
+    TGS_CUDA(cudaMemcpyAsync(dst, src, t.rec_floats * sizeof(float), cudaMemcpyHostToDevice, st));
+    t.stats.bytes_h2d += t.rec_floats * sizeof(float);
+  }
+  t.dirty_host[s] = 0;
+  t.stats.blocks_in++;
+}
+
+void Table::issue_early(Prepared& p) {
+  if (!cfg.overlap) TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
+  for (size_t i = 0; i < p.plan.early_block.size(); ++i) copy_block_in(*this, p.plan.early_block[i], p.plan.early_slot[i], h2d);
+  TGS_CUDA(cudaEventRecord(ev_h2d, h2d));
+}
+
+// Write-back of S- after the compute that used them (ev_comp must be the last
+// compute that may read those slots), then the loads into their slots.
+void Table::issue_evictions_and_late(Prepared& p) {
+  TGS_CUDA(cudaStreamWaitEvent(d2h, ev_comp, 0));
+  const uint64_t pf = (uint64_t)D * B;
+  for (size_t i = 0; i < p.plan.evict_block.size(); ++i) {
+    uint32_t b = p.plan.evict_block[i], s = p.plan.evict_slot[i];
+    if (dirty_host[s]) {
+      uint64_t nf = cfg.moments_policy == 1 ? pf : rec_floats;
+      TGS_CUDA(cudaMemcpyAsync(host + (uint64_t)b * rec_floats, pool + (uint64_t)s * rec_floats, nf * sizeof(float),
+                               cudaMemcpyDeviceToHost, d2h));
+      stats.bytes_d2h += nf * sizeof(float);
+      stats.writebacks++;
+    }
+    dirty_host[s] = 0;
+    TGS_CUDA(cudaEventRecord(slot_free_ev[s], d2h));
+    slot_has_ev[s] = 1;
+    stats.blocks_out++;
+  }
+  TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
+  for (size_t i = 0; i < p.plan.late_block.size(); ++i) copy_block_in(*this, p.plan.late_block[i], p.plan.late_slot[i], h2d);
+  TGS_CUDA(cudaEventRecord(ev_h2d, h2d));
+}
+
+void Table::collect_stall() {
+  if (!stall_pending) return;
+  TGS_CUDA(cudaEventSynchronize(ev_stall_b));
+  float ms = 0.f;
+  TGS_CUDA(cudaEventElapsedTime(&ms, ev_stall_a, ev_stall_b));
+  stats.stall_ms += ms;
+  stall_pending = false;
+}
+
+void Table::compute(const Prepared& p, const float* targets_dev, const float* targets_host, cudaStream_t user,
+                    bool backward, float* image_out) {
+  const uint32_t J = (uint32_t)p.cams.size();
+  const uint32_t n_items = (uint32_t)p.render_blocks.size();
+  TGS_CHECK(n_items <= max_items, TGS_ERR_CAPACITY, "render list exceeds the cache capacity");
+  const int W = (int)p.cams[0].width, H = (int)p.cams[0].height;
+  const uint64_t pix = (uint64_t)W * H;
+  collect_stall();
+  // wait for this batch's incoming blocks; the wait is the exposed copy time
+  TGS_CUDA(cudaEventRecord(ev_stall_a, comp));
+  TGS_CUDA(cudaStreamWaitEvent(comp, ev_h2d, 0));
+  TGS_CUDA(cudaEventRecord(ev_stall_b, comp));
+  stall_pending = true;
+  for (uint32_t j = 0; j < n_items; ++j) {
+    uint32_t b = p.render_blocks[j];
+    TGS_CHECK(slot_of[b] >= 0, TGS_ERR_STATE, "render block not resident");
+    rl_host[j] = (uint32_t)slot_of[b];
+    rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - (uint64_t)b * B);
+    rl_host[2ull * max_items + j] = b;
+  }
+  if (n_items) {
+    for (int q = 0; q < 3; ++q)
+      TGS_CUDA(cudaMemcpyAsync(rl_dev + (uint64_t)q * max_items, rl_host + (uint64_t)q * max_items,
+                               n_items * sizeof(uint32_t), cudaMemcpyHostToDevice, comp));
+  }
+  RenderList rl = render_list(n_items);
+  const uint64_t V = rl.capacity();
+  if (V) {
+    TGS_CUDA(cudaMemsetAsync(touched, 0, V, comp));
+    TGS_CUDA(cudaMemsetAsync(item_touched, 0, n_items * sizeof(uint32_t), comp));
+  }
+  for (uint32_t j = 0; j < J; ++j) {
+    DevCam dc = make_devcam(p.cams[j]);
+    float* img = image_out && J == 1 ? image_out : images + (uint64_t)j * pix * 3;
+    render_forward(rl, dc, cfg.bg, cams[j], img, touched, item_touched, comp);
+    stats.last_pairs = cams[j].n_pairs;
+    stats.last_visible = cams[j].n_vis;
+  }
+  stats.last_render_blocks = n_items;
+  if (backward) {
+    const float* tgt = targets_dev;
+    if (!tgt) {
+      TGS_CHECK(targets_host != nullptr, TGS_ERR_INVALID, "targets are required for a training step");
+      TGS_CUDA(cudaMemcpyAsync(targets_buf, targets_host, (uint64_t)J * pix * 3 * sizeof(float),
+                               cudaMemcpyHostToDevice, comp));
+      tgt = targets_buf;
+    } else {
+      TGS_CUDA(cudaEventRecord(ev_user, user));
+      TGS_CUDA(cudaStreamWaitEvent(comp, ev_user, 0));
+    }
+    TGS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), comp));
+    photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
+    if (V) TGS_CUDA(cudaMemsetAsync(grad_local, 0, (uint64_t)D * V * sizeof(float), comp));
+    for (uint32_t j = 0; j < J; ++j) {
+      DevCam dc = make_devcam(p.cams[j]);
+      render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
+      render_backward_params(rl, dc, cams[j], grad_local, false, comp);
+    }
+    mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp);
+    adam_render_list(rl, grad_local, touched, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp);
+    block_bounds(rl, item_touched, spheres, comp);
+    for (uint32_t j = 0; j < n_items; ++j) dirty_host[slot_of[p.render_blocks[j]]] = 1;
+    stats.steps++;
+  }
+  TGS_CUDA(cudaEventRecord(ev_comp, comp));
+  last_cams = p.cams;
+  last_render = p.render_blocks;
+  last_splus = p.s_plus;
+  last_sminus = p.s_minus;
+  last_kvis_host = p.kvis_host;
+  last_r_host = p.r_host;
+  if (user && !backward) {
+    TGS_CUDA(cudaEventRecord(ev_user, comp));
+    TGS_CUDA(cudaStreamWaitEvent(user, ev_user, 0));
+  }
+}
+
+static bool same_cams(const std::vector<tgs_camera>& a, const tgs_camera* b, uint32_t J) {
+  if (a.size() != J) return false;
+  return std::memcmp(a.data(), b, J * sizeof(tgs_camera)) == 0;
+}
+
+void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint32_t nJ, const float* targets_dev,
+                 const float* targets_host, cudaStream_t user, float* loss_out) {
+  TGS_CHECK(cs && J >= 1, TGS_ERR_INVALID, "tgs_step: no cameras");
+  if (!(prep.valid && same_cams(prep.cams, cs, J))) {
+    // reactive path: select and stream this batch's working set now
+    Prepared p;
+    prepare(cs, J, p);
+    issue_early(p);
+    issue_evictions_and_late(p);
+    prep = std::move(p);
+  }
+  Prepared cur = std::move(prep);
+  prep = Prepared();
+  Prepared nxt;
+  const bool prefetch = cfg.prefetch_mode == 1 && next && nJ >= 1;
+  if (prefetch) {
+    // Algorithm 1 for batch t+1 while batch t computes: selection uses the
+    // bounds as of the start of step t; incoming blocks go to spare slots now
+    prepare(next, nJ, nxt);
+    if (cfg.overlap) issue_early(nxt);
+  }
+  compute(cur, targets_dev, targets_host, user, true, nullptr);
+  if (prefetch) {
+    if (!cfg.overlap) issue_early(nxt);
+    issue_evictions_and_late(nxt);
+    prep = std::move(nxt);
+  }
+  if (loss_out) {
+    TGS_CUDA(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, comp));
+    TGS_CUDA(cudaStreamSynchronize(comp));
+    const uint32_t Jc = (uint32_t)cur.cams.size();
+    *loss_out = loss_host[0] / (float)((uint64_t)Jc * cur.cams[0].width * cur.cams[0].height * 3);
+  }
+  if (!cfg.overlap) TGS_CUDA(cudaStreamSynchronize(comp));
+}
+
+void Table::render(const tgs_camera& cam, float* image_dev, cudaStream_t user) {
+  Prepared p;
+  prepare(&cam, 1, p);
+  issue_early(p);
+  issue_evictions_and_late(p);
+  compute(p, nullptr, nullptr, user, false, image_dev);
+  prep = Prepared();
+}
+
+// Consistency barrier: every dirty resident block goes back to the host tier.
+void Table::flush() {
+  TGS_CUDA(cudaStreamSynchronize(comp));
+  TGS_CUDA(cudaStreamSynchronize(h2d));
+  TGS_CUDA(cudaStreamSynchronize(d2h));
+  const uint64_t pf = (uint64_t)D * B;
+  for (uint64_t s = 0; s < n_slots; ++s) {
+    int64_t b = block_of_slot[s];
+    if (b < 0 || !dirty_host[s]) continue;
+    uint64_t nf = cfg.moments_policy == 1 ? pf : rec_floats;
+    TGS_CUDA(cudaMemcpyAsync(host + (uint64_t)b * rec_floats, pool + s * rec_floats, nf * sizeof(float),
+                             cudaMemcpyDeviceToHost, d2h));
+    dirty_host[s] = 0;
+  }
+  TGS_CUDA(cudaStreamSynchronize(d2h));
+}
+
+}  // namespace tgs

@@ -1,0 +1,100 @@
+// The block-virtualised training table: pinned host tier, HBM working-set
+// cache, copy streams and the training step (Sec. 3.2-3.5).
+#pragma once
+#include <vector>
+
+#include "raster.cuh"
+#include "visibility.cuh"
+
+namespace tgs {
+
+struct CopyPlan {
+  std::vector<uint32_t> early_block, early_slot;  // into free slots, may start now
+  std::vector<uint32_t> evict_block, evict_slot;  // S-, after the compute that last used them
+  std::vector<uint32_t> late_block, late_slot;    // into slots freed by S-
+};
+
+struct Prepared {
+  bool valid = false;
+  std::vector<tgs_camera> cams;
+  std::vector<uint32_t> render_blocks;  // R & K of the batch, ascending
+  std::vector<uint32_t> s_plus, s_minus;
+  std::vector<uint32_t> kvis_host, r_host;  // per-camera visible sets, R after selection
+  CopyPlan plan;
+};
+
+struct Table {
+  tgs_config cfg{};
+  uint64_t N = 0, K = 0, words = 0;
+  uint32_t B = 0;
+  uint64_t C = 0, n_slots = 0;
+  uint64_t rec_floats = 0;   // floats per block record (params, m, v)
+  uint64_t V_cap = 0;        // render-list Gaussians capacity
+  uint32_t max_items = 0;
+
+  // host tier
+  float* host = nullptr;     // pinned, K records
+  std::vector<uint32_t> perm;
+
+  // device state
+  float* pool = nullptr;
+  float4* spheres = nullptr;
+  uint32_t* ages = nullptr;
+  uint32_t* block_step = nullptr;
+  uint8_t* dirty_dev = nullptr;
+  uint32_t *r_bits = nullptr, *r_next_bits = nullptr, *acc_bits = nullptr, *acc_next_bits = nullptr;
+  uint32_t *kvis = nullptr, *kvis_union = nullptr;  // of the last prepared batch
+  Planes* planes_dev = nullptr;
+  Planes* planes_host = nullptr;
+  ResidencyBuffers rb{};
+  uint32_t* lists_dev = nullptr;   // s_plus | s_minus | render (K each)
+  uint32_t* lists_host = nullptr;  // pinned
+  uint32_t* rl_dev = nullptr;      // item_slot | item_count | item_block
+  uint32_t* rl_host = nullptr;     // pinned
+  std::vector<CamState> cams;
+  float* images = nullptr;
+  float* dl_dimg = nullptr;
+  float* targets_buf = nullptr;
+  uint8_t* touched = nullptr;
+  uint32_t* item_touched = nullptr;
+  float* grad_local = nullptr;
+  float* loss_dev = nullptr;
+  float* loss_host = nullptr;
+
+  // host mirrors
+  std::vector<int64_t> slot_of;          // K
+  std::vector<int64_t> block_of_slot;    // n_slots
+  std::vector<uint8_t> dirty_host;       // n_slots
+  std::vector<cudaEvent_t> slot_free_ev; // n_slots (null = no pending use)
+  std::vector<uint8_t> slot_has_ev;
+
+  // last computed batch (for the debug getters)
+  std::vector<tgs_camera> last_cams;
+  std::vector<uint32_t> last_render, last_splus, last_sminus;
+  std::vector<uint32_t> last_kvis_host;  // J x words
+  std::vector<uint32_t> last_r_host;     // words
+  Prepared prep;
+
+  cudaStream_t comp = nullptr, h2d = nullptr, d2h = nullptr, ctl = nullptr;
+  cudaEvent_t ev_comp = nullptr, ev_h2d = nullptr, ev_ctl = nullptr, ev_user = nullptr;
+  cudaEvent_t ev_stall_a = nullptr, ev_stall_b = nullptr;
+  bool stall_pending = false;
+
+  tgs_stats stats{};
+
+  void create(const tgs_config& c, uint64_t n, const float* params_host);
+  void destroy();
+  void prepare(const tgs_camera* cams, uint32_t J, Prepared& out);
+  void issue_early(Prepared& p);
+  void issue_evictions_and_late(Prepared& p);
+  void compute(const Prepared& p, const float* targets_dev, const float* targets_host, cudaStream_t user,
+               bool backward, float* image_out);
+  void step(const tgs_camera* cams, uint32_t J, const tgs_camera* next, uint32_t nJ, const float* targets_dev,
+            const float* targets_host, cudaStream_t user, float* loss_out);
+  void render(const tgs_camera& cam, float* image_dev, cudaStream_t user);
+  void flush();
+  void collect_stall();
+  RenderList render_list(uint32_t n_items) const;
+};
+
+}  // namespace tgs
