@@ -298,6 +298,12 @@ void Table::prepare(const tgs_camera* cs, uint32_t J, Prepared& out) {
     slot_of[pl.late_block[i]] = pl.late_slot[i];
     block_of_slot[pl.late_slot[i]] = pl.late_block[i];
   }
+  out.render_slots.resize(out.render_blocks.size());
+  for (size_t j = 0; j < out.render_blocks.size(); ++j) {
+    int64_t s = slot_of[out.render_blocks[j]];
+    TGS_CHECK(s >= 0, TGS_ERR_STATE, "render block without a slot");
+    out.render_slots[j] = (uint32_t)s;
+  }
   out.valid = true;
 }
 
@@ -374,8 +380,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   stall_pending = true;
   for (uint32_t j = 0; j < n_items; ++j) {
     uint32_t b = p.render_blocks[j];
-    TGS_CHECK(slot_of[b] >= 0, TGS_ERR_STATE, "render block not resident");
-    rl_host[j] = (uint32_t)slot_of[b];
+    rl_host[j] = p.render_slots[j];
     rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - (uint64_t)b * B);
     rl_host[2ull * max_items + j] = b;
   }
@@ -420,7 +425,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp);
     adam_render_list(rl, grad_local, touched, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp);
     block_bounds(rl, item_touched, spheres, comp);
-    for (uint32_t j = 0; j < n_items; ++j) dirty_host[slot_of[p.render_blocks[j]]] = 1;
+    for (uint32_t j = 0; j < n_items; ++j) dirty_host[p.render_slots[j]] = 1;
     stats.steps++;
   }
   TGS_CUDA(cudaEventRecord(ev_comp, comp));

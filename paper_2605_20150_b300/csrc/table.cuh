@@ -18,6 +18,7 @@ struct Prepared {
   bool valid = false;
   std::vector<tgs_camera> cams;
   std::vector<uint32_t> render_blocks;  // R & K of the batch, ascending
+  std::vector<uint32_t> render_slots;   // their slots, fixed when the batch is selected
   std::vector<uint32_t> s_plus, s_minus;
   std::vector<uint32_t> kvis_host, r_host;  // per-camera visible sets, R after selection
   CopyPlan plan;

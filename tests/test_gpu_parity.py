@@ -1,0 +1,146 @@
+"""GPU parity of the training step against the FP64 oracle, through the C ABI.
+
+Small-cube workload: 20,000 Gaussians in 16 Morton blocks of 1,250, 256x256
+cameras (16 x 16 tiles, several tiles per Gaussian, ragged last block when
+n is not a multiple of B).  Tolerances: block order, visibility sets, deltas
+and the tile/depth order bit-exact; projected centre and depth bit-exact (both
+sides follow the FP32 key-path specification); images max-abs 1e-4 plus the
+oracle's slack at pixels whose result depends on a borderline FP32 decision;
+gradients rel-L2 1e-3."""
+import numpy as np
+import pytest
+
+import scenes
+from parity_util import c1_inputs, image_within, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(orc, tgs, loss=1, n=20000, block_size=1250, **cfg):
+    c, perm, Pm, tp = c1_inputs(orc, block_size=block_size, n=n)
+    cams = [scenes.camera_array(x) for x in c["cams"]]
+    _, Pt = orc.create(tp, block_size)
+    targets = [orc.render(Pt.astype(np.float64), cam)["img"].astype(np.float32) for cam in cams]
+    table = tgs.TideTable(c["params"], block_size=block_size, max_batch=2, max_width=256, max_height=256, loss=loss,
+                          **cfg)
+    return c, perm, Pm, cams, targets, table
+
+
+def test_create_block_order_and_spheres(orc, tgs):
+    c, perm, Pm, cams, targets, table = _setup(orc, tgs)
+    assert np.array_equal(table.block_order(), perm)
+    sph_o = orc.block_spheres(Pm.astype(np.float64), 1250)
+    sph_g = table.spheres()
+    np.testing.assert_allclose(sph_g, sph_o, rtol=2e-6, atol=2e-6)
+    table.close()
+
+
+@pytest.mark.parametrize("loss", [1, 0])
+def test_step_matches_oracle(orc, tgs, loss):
+    c, perm, Pm, cams, targets, table = _setup(orc, tgs, loss=loss)
+    B, K = 1250, 16
+    lval = table.step([c["cams"][0]], targets[0][None])
+    # ---- oracle: the same step over the render set R & K
+    P = Pm.astype(np.float64).copy()
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    steps = np.zeros(K, np.int64)
+    sph = orc.block_spheres(Pm.astype(np.float64), B)
+    _, vis = orc.visible_blocks(sph, [cams[0]])
+    sets = table.sets(1)
+    assert np.array_equal(sets["k_visible"], vis)
+    render_blocks = np.nonzero(vis & sets["r_resident"])[0]
+    o = orc.train_step(P, M1, M2, steps, B, render_blocks, [cams[0]], targets[0][None], lr=1e-3, loss_kind=loss)
+    assert abs(lval - o["loss"]) <= 1e-4 * o["loss"]
+    # ---- forward intermediates
+    rec = table.camera_record(0, 256, 256)
+    orec = o["records"][0]
+    assert np.array_equal(rec["ids"], o["ids"])
+    S = orec["S"]
+    vg = rec["splat"][:, 11] != 0
+    vo = S[:, orc.VISIBLE] != 0
+    border = S[:, orc.BORDER] != 0
+    assert np.array_equal(vg[~border], vo[~border])
+    both = vg & vo
+    for col, name in ((0, "u"), (1, "v"), (2, "depth")):
+        assert np.array_equal(rec["splat"][both, col], S[both, col].astype(np.float32)), name
+    nb = both & ~border
+    assert np.array_equal(rec["splat"][nb, 10], S[nb, orc.RADIUS])
+    assert np.array_equal(rec["rect"][nb], S[nb][:, [orc.X0, orc.Y0, orc.X1, orc.Y1]].astype(np.int32))
+    for col in (3, 4, 5, 6, 7, 8, 9):
+        np.testing.assert_allclose(rec["splat"][both, col], S[both, col], rtol=2e-4, atol=2e-5)
+    # sort order: per tile, identical sequences unless a border Gaussian is involved
+    bset = set(np.nonzero(border)[0].tolist())
+    for t in range(rec["ranges"].shape[0]):
+        a, b = rec["ranges"][t]
+        oa, ob = orec["ranges"][t]
+        sg, so = rec["pair_vals"][a:b], orec["vals"][oa:ob]
+        if bset & (set(sg.tolist()) | set(so.tolist())):
+            continue
+        assert np.array_equal(sg, so), t
+    err, frac = image_within(rec["image"], orec)
+    assert err <= 1e-4 and frac < 0.05
+    clean = orec["slack"] == 0
+    np.testing.assert_allclose(rec["t_final"][clean], orec["T"][clean], atol=1e-5)
+    assert np.array_equal(rec["n_last"][clean], orec["nlast"][clean])
+    # ---- gradients: 2D record and the 59-parameter gradient (from m = (1 - b1) g)
+    if loss == 1:
+        g2o = o["g2"][0]
+        for q in range(9):
+            assert rel_l2(rec["grad2d"][vo & vg, q], g2o[vo & vg, q]) < 1e-3, q
+    p_g, m1, m2, st = table.state()
+    touched = o["touched"].astype(bool)
+    ids = o["ids"]
+    g_gpu = m1[ids] / 0.1
+    g_o = o["grad"]
+    if loss == 1:
+        assert rel_l2(g_gpu[touched], g_o[touched]) < 1e-3
+        for f in range(59):
+            assert rel_l2(g_gpu[touched, f], g_o[touched, f]) < 1e-3, f
+    else:
+        assert rel_l2(g_gpu[touched], g_o[touched]) < 2e-2
+    # ---- masked Adam: untouched rows bit-identical, touched rows moved like the oracle
+    assert np.array_equal(p_g[~np.isin(np.arange(len(p_g)), ids[touched])],
+                          Pm[~np.isin(np.arange(len(p_g)), ids[touched])])
+    assert np.array_equal(st, steps.astype(np.uint32))
+    if loss == 1:
+        d_g = p_g[ids].astype(np.float64) - Pm[ids].astype(np.float64)
+        d_o = P[ids] - Pm[ids].astype(np.float64)
+        scale = np.abs(g_o[touched]).max(0)
+        amb = np.abs(g_o) < 1e-4 * scale
+        ok = np.abs(d_g - d_o) <= 1e-6 + 2.1e-3 * amb
+        assert ok[touched].all()
+    table.close()
+
+
+def test_block_delta_two_cameras(orc, tgs):
+    """Capacity 8 of 16 blocks, two close cameras: R, S+ and S- follow
+    Algorithm 1 exactly (exact next-batch prefetch)."""
+    cfg = scenes.small_cube_config()
+    perm, Pm = orc.create(cfg["params"], 1250)
+    camsd = []
+    for pos, tgt in (([0.0, 0.0, -1.4], [0.5, 0.4, 0.0]), ([0.3, 0.1, -1.4], [0.9, 0.3, 0.2]),
+                     ([0.7, 0.2, -1.2], [1.0, -0.2, 0.4])):
+        R, t = scenes.look_at(pos, tgt)
+        camsd.append(scenes.pinhole(256, 256, 50.0, R, t))
+    cams = [scenes.camera_array(x) for x in camsd]
+    table = tgs.TideTable(cfg["params"], block_size=1250, max_batch=1, max_width=256, max_height=256,
+                          cache_blocks=8, spare_slots=2, prefetch_mode=1, lr=0.0)
+    tgt = np.zeros((1, 256, 256, 3), np.float32)
+    sph = orc.block_spheres(Pm.astype(np.float64), 1250)
+    K = 16
+    r = np.zeros(K, np.uint8)
+    kacc = np.zeros(K, np.uint8)
+    age = np.full(K, 126, np.uint32)
+    for i in range(3):
+        nxt = [camsd[i + 1]] if i + 1 < 3 else None
+        table.step([camsd[i]], tgt, next_cams=nxt)
+        vis, _ = orc.visible_blocks(sph, [cams[i]])
+        out = orc.residency(kacc, vis[None] if vis.ndim == 1 else vis, r, age, 8, 0.75, 8 // 2)
+        sets = table.sets(1)
+        assert np.array_equal(sets["k_visible"], vis.reshape(-1)), i
+        assert np.array_equal(sets["r_resident"], out["r_next"]), i
+        assert sets["s_plus"].tolist() == out["s_plus"].tolist(), i
+        assert sets["s_minus"].tolist() == out["s_minus"].tolist(), i
+        kacc = (out["r_next"] & vis.reshape(-1)).astype(np.uint8)
+        r, age = out["r_next"], out["age"]
+    table.close()
