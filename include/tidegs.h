@@ -182,6 +182,16 @@ typedef struct tgs_stats {
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
 
+/* Stage timing (tracing): when enabled, CUDA events on the compute stream
+ * bracket each stage of every step.  Stages, in order: 0 Level-2 preprocess,
+ * 1 binning + depth/tile sort, 2 forward raster, 3 loss, 4 backward raster,
+ * 5 backward preprocess, 6 masked Adam, 7 bound refresh.
+ * tgs_get_stage_ms waits for the recorded events and returns the accumulated
+ * milliseconds and launch counts per stage (8 values each); reset = 1 clears
+ * the accumulators after reading. */
+tgs_status tgs_set_stage_timing(tgs_table* t, int enable);
+tgs_status tgs_get_stage_ms(tgs_table* t, double* ms8, uint64_t* counts8, int reset);
+
 /* ---------------------------------------------------------------------------
  * Resident (fully in-HBM) rasteriser for autograd frameworks: the standard
  * 3DGS forward/backward that Sec. 3.3 "Level 2" runs on the resident blocks.

@@ -71,6 +71,8 @@ _SIGS = {
     "tgs_get_camera_record": (ctypes.c_int32, [_VP, _U32, ctypes.POINTER(_U64), ctypes.POINTER(_U64), _VP, _VP, _VP,
                                                _VP, _VP, _VP, _VP, _VP, _VP]),
     "tgs_get_stats": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_stats)]),
+    "tgs_set_stage_timing": (ctypes.c_int32, [_VP, ctypes.c_int]),
+    "tgs_get_stage_ms": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int]),
     "tgs_raster_create": (ctypes.c_int32, [_U64, _U32, _U32, ctypes.POINTER(_VP)]),
     "tgs_raster_destroy": (None, [_VP]),
     "tgs_raster_forward": (ctypes.c_int32, [_VP, _VP, _U64, _U32, ctypes.POINTER(tgs_camera), _VP, _VP, _VP]),
@@ -251,6 +253,17 @@ class TideTable:
                                          _ptr(r["grad2d"])))
         r["pair_vals"] = r["pair_vals"][:m]
         return r
+
+    STAGES = ("preprocess", "sort", "raster_fwd", "loss", "raster_bwd", "preprocess_bwd", "adam", "bounds")
+
+    def stage_timing(self, on=True):
+        _check(load().tgs_set_stage_timing(self.h, int(on)))
+
+    def stage_ms(self, reset=False):
+        ms = np.zeros(8, np.float64)
+        cnt = np.zeros(8, np.uint64)
+        _check(load().tgs_get_stage_ms(self.h, _ptr(ms), _ptr(cnt), int(reset)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.STAGES)}
 
     def stats(self):
         s = tgs_stats()

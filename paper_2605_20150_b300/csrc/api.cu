@@ -337,6 +337,25 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out) {
   });
 }
 
+tgs_status tgs_set_stage_timing(tgs_table* t, int enable) {
+  return guard([&] {
+    TGS_CHECK(t, TGS_ERR_INVALID, "tgs_set_stage_timing: null table");
+    t->t.timer.on = enable != 0;
+  });
+}
+
+tgs_status tgs_get_stage_ms(tgs_table* t, double* ms8, uint64_t* counts8, int reset) {
+  return guard([&] {
+    TGS_CHECK(t, TGS_ERR_INVALID, "tgs_get_stage_ms: null table");
+    t->t.timer.collect();
+    for (int i = 0; i < StageTimer::NSTAGE; ++i) {
+      if (ms8) ms8[i] = t->t.timer.ms[i];
+      if (counts8) counts8[i] = t->t.timer.count[i];
+    }
+    if (reset) t->t.timer.reset();
+  });
+}
+
 tgs_status tgs_raster_create(uint64_t max_gaussians, uint32_t max_width, uint32_t max_height, tgs_raster** out) {
   return guard([&] {
     TGS_CHECK(out && max_gaussians > 0 && max_width > 0 && max_height > 0, TGS_ERR_INVALID,

@@ -818,7 +818,9 @@ static int bits_for(uint64_t n) {
 }
 
 void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
-                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s) {
+                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s, StageTimer* tm) {
+  StageTimer dummy;
+  if (!tm) tm = &dummy;
   const uint64_t V = rl.capacity();
   TGS_CHECK(V <= cs.cap_v, TGS_ERR_CAPACITY, "render list exceeds the per-camera capacity");
   TGS_CHECK((uint64_t)cam.W * cam.H <= cs.cap_pix && (uint64_t)cam.TX * cam.TY <= cs.cap_tiles, TGS_ERR_CAPACITY,
@@ -832,8 +834,11 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   if (V > 0) {
     unsigned cpi = div_up(rl.B, PP_THREADS);
     PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
+    tm->begin(StageTimer::PRE, s);
     k_preprocess<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
     TGS_LAUNCHED();
+    tm->end(StageTimer::PRE, s);
+    tm->begin(StageTimer::SORT, s);
     exclusive_scan_u32(cs.scan, cs.scan, cs.counters, V, cs.scratch, s);
     k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
     TGS_LAUNCHED();
@@ -861,9 +866,12 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
       TGS_LAUNCHED();
     }
   }
+  tm->end(StageTimer::SORT, s);
+  tm->begin(StageTimer::FWD, s);
   k_raster_fwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last);
   TGS_LAUNCHED();
+  tm->end(StageTimer::FWD, s);
 }
 
 void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,

@@ -3,6 +3,7 @@
 // run over the Gaussians of a render list of resident blocks.
 #pragma once
 #include "common.cuh"
+#include "stage_timer.cuh"
 
 namespace tgs {
 
@@ -65,7 +66,7 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
 // gets 1 for items with a visible Gaussian.  Synchronises the stream twice
 // to read the visible and pair counts.
 void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
-                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s);
+                    uint8_t* touched, uint32_t* item_touched, cudaStream_t s, StageTimer* tm = nullptr);
 
 // Backward of the compositing into cs.g2 (zeroed here).
 void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,

@@ -398,7 +398,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   for (uint32_t j = 0; j < J; ++j) {
     DevCam dc = make_devcam(p.cams[j]);
     float* img = image_out && J == 1 ? image_out : images + (uint64_t)j * pix * 3;
-    render_forward(rl, dc, cfg.bg, cams[j], img, touched, item_touched, comp);
+    render_forward(rl, dc, cfg.bg, cams[j], img, touched, item_touched, comp, &timer);
     stats.last_pairs = cams[j].n_pairs;
     stats.last_visible = cams[j].n_vis;
   }
@@ -415,30 +415,37 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
       TGS_CUDA(cudaStreamWaitEvent(comp, ev_user, 0));
     }
     TGS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), comp));
+    timer.begin(StageTimer::LOSS, comp);
     photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
+    timer.end(StageTimer::LOSS, comp);
     if (V) TGS_CUDA(cudaMemsetAsync(grad_local, 0, (uint64_t)D * V * sizeof(float), comp));
     for (uint32_t j = 0; j < J; ++j) {
       DevCam dc = make_devcam(p.cams[j]);
+      timer.begin(StageTimer::BWD, comp);
       render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
+      timer.end(StageTimer::BWD, comp);
+      timer.begin(StageTimer::PBWD, comp);
       render_backward_params(rl, dc, cams[j], grad_local, false, comp);
+      timer.end(StageTimer::PBWD, comp);
     }
+    timer.begin(StageTimer::ADAM, comp);
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp);
     adam_render_list(rl, grad_local, touched, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp);
+    timer.end(StageTimer::ADAM, comp);
+    timer.begin(StageTimer::BOUNDS, comp);
     block_bounds(rl, item_touched, spheres, comp);
+    timer.end(StageTimer::BOUNDS, comp);
     for (uint32_t j = 0; j < n_items; ++j) dirty_host[p.render_slots[j]] = 1;
     stats.steps++;
   }
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
+  if (user) TGS_CUDA(cudaStreamWaitEvent(user, ev_comp, 0));
   last_cams = p.cams;
   last_render = p.render_blocks;
   last_splus = p.s_plus;
   last_sminus = p.s_minus;
   last_kvis_host = p.kvis_host;
   last_r_host = p.r_host;
-  if (user && !backward) {
-    TGS_CUDA(cudaEventRecord(ev_user, comp));
-    TGS_CUDA(cudaStreamWaitEvent(user, ev_user, 0));
-  }
 }
 
 static bool same_cams(const std::vector<tgs_camera>& a, const tgs_camera* b, uint32_t J) {

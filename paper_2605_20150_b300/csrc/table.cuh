@@ -82,6 +82,7 @@ struct Table {
   bool stall_pending = false;
 
   tgs_stats stats{};
+  StageTimer timer;
 
   void create(const tgs_config& c, uint64_t n, const float* params_host);
   void destroy();
