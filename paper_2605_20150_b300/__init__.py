@@ -78,6 +78,7 @@ _SIGS = {
     "tgs_raster_forward": (ctypes.c_int32, [_VP, _VP, _U64, _U32, ctypes.POINTER(tgs_camera), _VP, _VP, _VP]),
     "tgs_raster_backward": (ctypes.c_int32, [_VP, _VP, _U64, _U32, ctypes.POINTER(tgs_camera), _VP, _VP, _VP, _VP,
                                              _VP]),
+    "tgs_raster_forward_noalloc": (ctypes.c_int32, [_VP, _U64, _U32, ctypes.POINTER(tgs_camera), _VP, _VP, _VP]),
     "tgs_adam": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP, _VP, _U64, _U32, _F, _F, _F, _F, _VP]),
 }
 
@@ -355,6 +356,14 @@ def rasterize(blocks, n, cam, bg, rasterizer):
     if _GR is None:
         _GR = _autograd_fn()
     return _GR.apply(blocks, n, cam, tuple(bg), rasterizer)
+
+
+def raster_forward_noalloc(blocks, n, cam, bg, image):
+    """tgs_raster_forward_noalloc: the forward render without any device
+    allocation (fixed 16 MiB static scratch; see include/tidegs.h for limits)."""
+    bgc = (ctypes.c_float * 3)(*bg)
+    _check(load().tgs_raster_forward_noalloc(_ptr(blocks), n, blocks.shape[2], ctypes.byref(make_camera(cam)), bgc,
+                                             _ptr(image), _stream()))
 
 
 def adam(blocks, grad, m1, m2, touched, steps, n, lr=1e-3, b1=0.9, b2=0.999, eps=1e-15):

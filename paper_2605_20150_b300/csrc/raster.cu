@@ -874,6 +874,59 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   tm->end(StageTimer::FWD, s);
 }
 
+// The forward of render_forward on caller-provided fixed buffers: nothing is
+// (re)allocated; a pair count above cs.cap_pairs is an error.  Counts are read
+// back into host stack variables.
+void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
+                          cudaStream_t s) {
+  const uint64_t V = rl.capacity();
+  TGS_CHECK(V <= cs.cap_v, TGS_ERR_CAPACITY, "render list exceeds the fixed capacity");
+  TGS_CHECK((uint64_t)cam.W * cam.H <= cs.cap_pix && (uint64_t)cam.TX * cam.TY <= cs.cap_tiles, TGS_ERR_CAPACITY,
+            "image larger than the fixed maximum");
+  cs.W = cam.W; cs.H = cam.H; cs.TX = cam.TX; cs.TY = cam.TY;
+  const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
+  const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
+  cs.n_vis = 0;
+  cs.n_pairs = 0;
+  uint32_t cnt = 0;
+  TGS_CUDA(cudaMemsetAsync(cs.ranges, 0, tiles * sizeof(uint2), s));
+  if (V > 0) {
+    unsigned cpi = div_up(rl.B, PP_THREADS);
+    PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
+    k_preprocess<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, nullptr, nullptr, cpi);
+    TGS_LAUNCHED();
+    exclusive_scan_u32(cs.scan, cs.scan, cs.counters, V, cs.scratch, s);
+    k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
+    TGS_LAUNCHED();
+    TGS_CUDA(cudaMemcpyAsync(&cnt, cs.counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TGS_CUDA(cudaStreamSynchronize(s));
+    cs.n_vis = cnt;
+  }
+  const uint64_t nv = cs.n_vis;
+  if (nv > 0) {
+    radix_sort_pairs(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv, 32, cs.scratch, s);
+    k_gather_counts<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.ntiles, cs.scan);
+    TGS_LAUNCHED();
+    exclusive_scan_u32(cs.scan, cs.scan, cs.counters + 1, nv, cs.scratch, s);
+    TGS_CUDA(cudaMemcpyAsync(&cnt, cs.counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TGS_CUDA(cudaStreamSynchronize(s));
+    cs.n_pairs = cnt;
+    TGS_CHECK(cs.n_pairs <= cs.cap_pairs, TGS_ERR_CAPACITY, "tile/Gaussian pairs exceed the fixed maximum");
+    const uint64_t np = cs.n_pairs;
+    if (np > 0) {
+      k_emit_pairs<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys, cs.pvals);
+      TGS_LAUNCHED();
+      radix_sort_pairs(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np,
+                       bits_for(tiles), cs.scratch, s);
+      k_ranges<<<div_up(np, 256), 256, 0, s>>>(np, cs.pkeys, cs.ranges);
+      TGS_LAUNCHED();
+    }
+  }
+  k_raster_fwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+                                                   cam.TX, bg3, image, cs.t_final, cs.n_last);
+  TGS_LAUNCHED();
+}
+
 void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,
                         const float* dl_dimage, cudaStream_t s) {
   const uint64_t V = rl.capacity();

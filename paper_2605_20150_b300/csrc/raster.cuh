@@ -68,6 +68,11 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
 void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
                     uint8_t* touched, uint32_t* item_touched, cudaStream_t s, StageTimer* tm = nullptr);
 
+// render_forward on fixed caller-provided buffers (no allocation; pairs
+// beyond cs.cap_pairs are a TGS_ERR_CAPACITY error).
+void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
+                          cudaStream_t s);
+
 // Backward of the compositing into cs.g2 (zeroed here).
 void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,
                         const float* dl_dimage, cudaStream_t s);
