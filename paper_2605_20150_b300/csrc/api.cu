@@ -408,7 +408,7 @@ tgs_status tgs_raster_backward(tgs_raster* r, const float* params_dev, uint64_t 
     TGS_CHECK(dc.W == r->r.cs.W && dc.H == r->r.cs.H, TGS_ERR_STATE, "backward camera differs from the forward");
     render_backward_2d(rl, dc, bg, r->r.cs, dl_dimage_dev, s);
     // grad_dev shares the parameters' block layout
-    render_backward_params(rl, dc, r->r.cs, grad_dev, true, s);
+    render_backward_params(rl, dc, r->r.cs, grad_dev, 2, s);
     if (touched_dev) mark_visible_bytes(rl, r->r.cs, touched_dev, s);
   });
 }

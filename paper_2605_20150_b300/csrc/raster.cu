@@ -9,7 +9,7 @@
 //  emission in depth order + stable tile sort (the tile/depth order of the
 //  pairs equals a stable sort of (tile << 32 | depth bits) keys emitted in id
 //  order, with far fewer radix passes over the pairs).
-//  k_raster_fwd      one CTA per 16x16 tile, batches of 256 splats staged in
+//  k_raster_fwd      one CTA per 16x16 tile (64 threads x 4 pixels), 128 splats staged in
 //                    shared memory, front-to-back blending with the 0.99 clamp,
 //                    the 1/255 skip and the T < 1e-4 stop.
 //  k_raster_bwd      reverse traversal from each pixel's last contributor,
@@ -252,67 +252,134 @@ __global__ void k_ranges(uint64_t np, const uint32_t* __restrict__ pkeys, uint2*
   if (p == np - 1 || pkeys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
 }
 
-__global__ void __launch_bounds__(TILE_PIX) k_raster_fwd(const uint2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ pvals,
-                                                        const float2* __restrict__ xy,
-                                                        const float4* __restrict__ conic_o,
-                                                        const float4* __restrict__ rgb, int W, int H, int TX,
-                                                        float3 bg, float* __restrict__ img,
-                                                        float* __restrict__ t_final, int* __restrict__ n_last) {
-  __shared__ float2 s_xy[TILE_PIX];
-  __shared__ float4 s_co[TILE_PIX];
-  __shared__ float4 s_rgb[TILE_PIX];
+// Raster CTA: one 16x16 tile, 128 threads in 4 warps; each warp owns an 8x8
+// pixel square and each thread two vertically adjacent pixels of it.  Splats
+// are staged R_BATCH at a time in shared memory together with the half-sizes
+// of the box outside which their alpha is certainly below 1/255; a warp whose
+// square misses that box skips the splat (a warp-uniform branch, so results
+// are unchanged), otherwise each thread evaluates its pixels with predicated,
+// branch-free updates.
+constexpr int R_PPT = 2;
+constexpr int R_THREADS = TILE_PIX / R_PPT;  // 128
+constexpr int R_BATCH = 128;
+
+struct WarpPix {
+  int px, py0;     // this thread's column and first row
+  float wx0, wy0;  // the warp square's first column and row
+};
+__device__ __forceinline__ WarpPix warp_pixels(int tile, int TX) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  WarpPix q;
+  const int x0 = (tile % TX) * TILE + (w & 1) * 8;
+  const int y0 = (tile / TX) * TILE + (w >> 1) * 8;
+  q.px = x0 + (l & 7);
+  q.py0 = y0 + (l >> 3) * R_PPT;
+  q.wx0 = (float)x0;
+  q.wy0 = (float)y0;
+  return q;
+}
+
+// Half-sizes of the axis-aligned box containing every pixel offset d with
+// alpha >= 1/255: d^T K d <= 2 ln(255 o) with K the conic (A, B, C), so
+// |dx| <= sqrt(2 L (K^-1)_xx).  Widened by a relative 1e-3 and 0.05 px; a
+// negative value means the splat can never reach 1/255.
+__device__ __forceinline__ float2 alpha_box(float A, float B, float C, float o) {
+  const float L = logf(255.f * o);
+  if (!(L > 0.f)) return make_float2(-1.f, -1.f);
+  const float det = A * C - B * B;
+  const float s = 2.002f * L / det;
+  return make_float2(sqrtf(fmaxf(s * C, 0.f)) + 0.05f, sqrtf(fmaxf(s * A, 0.f)) + 0.05f);
+}
+
+__device__ __forceinline__ bool warp_misses(const WarpPix& q, float x, float y, float2 h) {
+  return h.x < 0.f || x + h.x < q.wx0 || x - h.x > q.wx0 + 7.f || y + h.y < q.wy0 || y - h.y > q.wy0 + 7.f;
+}
+
+__global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ pvals,
+                                                         const float2* __restrict__ xy,
+                                                         const float4* __restrict__ conic_o,
+                                                         const float4* __restrict__ rgb, int W, int H, int TX,
+                                                         float3 bg, float* __restrict__ img,
+                                                         float* __restrict__ t_final, int* __restrict__ n_last) {
+  __shared__ float4 s_a[R_BATCH];  // x, y, A, B
+  __shared__ float4 s_b[R_BATCH];  // C, opacity, r, g
+  __shared__ float s_c[R_BATCH];   // b
+  __shared__ float2 s_h[R_BATCH];  // alpha box half-sizes
   const int tile = blockIdx.x;
-  const int px = (tile % TX) * TILE + (threadIdx.x & 15);
-  const int py = (tile / TX) * TILE + (threadIdx.x >> 4);
-  const bool inside = px < W && py < H;
+  const WarpPix q = warp_pixels(tile, TX);
   const uint2 r = ranges[tile];
   const int n = (int)(r.y - r.x);
-  const float fpx = (float)px, fpy = (float)py;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  int last = 0;
-  bool done = !inside;
-  for (int b = 0; b < n; b += TILE_PIX) {
-    if (__syncthreads_count(done) == TILE_PIX) break;
-    int k = b + threadIdx.x;
-    if (k < n) {
-      uint32_t id = pvals[r.x + k];
-      s_xy[threadIdx.x] = xy[id];
-      s_co[threadIdx.x] = conic_o[id];
-      s_rgb[threadIdx.x] = rgb[id];
+  const float fpx = (float)q.px;
+  float T[R_PPT], C0[R_PPT], C1[R_PPT], C2[R_PPT];
+  int last[R_PPT];
+  bool live[R_PPT];
+#pragma unroll
+  for (int k = 0; k < R_PPT; ++k) {
+    T[k] = 1.f;
+    C0[k] = C1[k] = C2[k] = 0.f;
+    last[k] = 0;
+    live[k] = q.px < W && q.py0 + k < H;
+  }
+  for (int b = 0; b < n; b += R_BATCH) {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < R_PPT; ++k) any |= live[k];
+    if (__syncthreads_count(any) == 0) break;
+    for (int t = threadIdx.x; t < R_BATCH; t += R_THREADS) {
+      int k = b + t;
+      if (k < n) {
+        uint32_t id = pvals[r.x + k];
+        float2 g = xy[id];
+        float4 co = conic_o[id];
+        float4 cc = rgb[id];
+        s_a[t] = make_float4(g.x, g.y, co.x, co.y);
+        s_b[t] = make_float4(co.z, co.w, cc.x, cc.y);
+        s_c[t] = cc.z;
+        s_h[t] = alpha_box(co.x, co.y, co.z, co.w);
+      }
     }
     __syncthreads();
-    const int m = min(TILE_PIX, n - b);
-    for (int j = 0; !done && j < m; ++j) {
-      float2 g = s_xy[j];
-      float4 co = s_co[j];
-      float dx, dy;
-      float power = splat_power(fpx, fpy, g.x, g.y, co.x, co.y, co.z, dx, dy);
-      if (power > 0.f) continue;
-      float G;
-      float alpha = splat_alpha(co.w, power, G);
-      if (alpha < ALPHA_MIN) continue;
-      float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-      if (Tn < T_STOP) {
-        done = true;
-        break;
+    const int m = min(R_BATCH, n - b);
+    for (int j = 0; j < m; ++j) {
+      const float4 a = s_a[j];
+      if (warp_misses(q, a.x, a.y, s_h[j])) continue;
+      const float4 bb = s_b[j];
+      const float cb = s_c[j];
+      bool act = false;
+#pragma unroll
+      for (int k = 0; k < R_PPT; ++k) {
+        float dx, dy;
+        const float power = splat_power(fpx, (float)(q.py0 + k), a.x, a.y, a.z, a.w, bb.x, dx, dy);
+        float G;
+        const float alpha = splat_alpha(bb.y, power, G);
+        const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+        const bool ok = live[k] && power <= 0.f && alpha >= ALPHA_MIN;
+        const bool stop = ok && Tn < T_STOP;
+        const bool take = ok && !stop;
+        live[k] = live[k] && !stop;
+        const float w = take ? alpha * T[k] : 0.f;
+        C0[k] += bb.z * w;
+        C1[k] += bb.w * w;
+        C2[k] += cb * w;
+        T[k] = take ? Tn : T[k];
+        last[k] = take ? b + j + 1 : last[k];
+        act |= live[k];
       }
-      float4 cc = s_rgb[j];
-      float w = alpha * T;
-      C0 += cc.x * w;
-      C1 += cc.y * w;
-      C2 += cc.z * w;
-      T = Tn;
-      last = b + j + 1;
+      if (!__any_sync(0xffffffffu, act)) break;
     }
   }
-  if (inside) {
-    uint64_t pix = (uint64_t)py * W + px;
-    img[3 * pix + 0] = C0 + T * bg.x;
-    img[3 * pix + 1] = C1 + T * bg.y;
-    img[3 * pix + 2] = C2 + T * bg.z;
-    t_final[pix] = T;
-    n_last[pix] = last;
+#pragma unroll
+  for (int k = 0; k < R_PPT; ++k) {
+    const int py = q.py0 + k;
+    if (q.px < W && py < H) {
+      uint64_t pix = (uint64_t)py * W + q.px;
+      img[3 * pix + 0] = C0[k] + T[k] * bg.x;
+      img[3 * pix + 1] = C1[k] + T[k] * bg.y;
+      img[3 * pix + 2] = C2[k] + T[k] * bg.z;
+      t_final[pix] = T[k];
+      n_last[pix] = last[k];
+    }
   }
 }
 
@@ -322,126 +389,134 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(TILE_PIX) k_raster_bwd(const uint2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ pvals,
-                                                        const float2* __restrict__ xy,
-                                                        const float4* __restrict__ conic_o,
-                                                        const float4* __restrict__ rgb, int W, int H, int TX,
-                                                        float3 bg, const float* __restrict__ t_final,
-                                                        const int* __restrict__ n_last,
-                                                        const float* __restrict__ dl_dimg, float* __restrict__ g2,
-                                                        uint64_t V) {
-  __shared__ uint32_t s_id[TILE_PIX];
-  __shared__ float2 s_xy[TILE_PIX];
-  __shared__ float4 s_co[TILE_PIX];
-  __shared__ float4 s_rgb[TILE_PIX];
+__global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ pvals,
+                                                         const float2* __restrict__ xy,
+                                                         const float4* __restrict__ conic_o,
+                                                         const float4* __restrict__ rgb, int W, int H, int TX,
+                                                         float3 bg, const float* __restrict__ t_final,
+                                                         const int* __restrict__ n_last,
+                                                         const float* __restrict__ dl_dimg, float* __restrict__ g2,
+                                                         uint64_t V) {
+  __shared__ uint32_t s_id[R_BATCH];
+  __shared__ float4 s_a[R_BATCH];
+  __shared__ float4 s_b[R_BATCH];
+  __shared__ float s_c[R_BATCH];
+  __shared__ float2 s_h[R_BATCH];
   __shared__ int s_max;
   const int tile = blockIdx.x;
-  const int px = (tile % TX) * TILE + (threadIdx.x & 15);
-  const int py = (tile / TX) * TILE + (threadIdx.x >> 4);
-  const bool inside = px < W && py < H;
+  const WarpPix q = warp_pixels(tile, TX);
   const uint2 r = ranges[tile];
-  const uint64_t pix = (uint64_t)py * W + px;
-  float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
-  int last = 0;
-  if (inside) {
-    T = t_final[pix];
-    last = n_last[pix];
-    gr = dl_dimg[3 * pix + 0];
-    gg = dl_dimg[3 * pix + 1];
-    gb = dl_dimg[3 * pix + 2];
+  const float fpx = (float)q.px;
+  float T[R_PPT], gr[R_PPT], gg[R_PPT], gb[R_PPT], S0[R_PPT], S1[R_PPT], S2[R_PPT], tfb[R_PPT];
+  int last[R_PPT];
+  int mylast = 0;
+#pragma unroll
+  for (int k = 0; k < R_PPT; ++k) {
+    const int py = q.py0 + k;
+    T[k] = 1.f;
+    last[k] = 0;
+    gr[k] = gg[k] = gb[k] = 0.f;
+    S0[k] = S1[k] = S2[k] = 0.f;
+    if (q.px < W && py < H) {
+      const uint64_t pix = (uint64_t)py * W + q.px;
+      T[k] = t_final[pix];
+      last[k] = n_last[pix];
+      gr[k] = dl_dimg[3 * pix + 0];
+      gg[k] = dl_dimg[3 * pix + 1];
+      gb[k] = dl_dimg[3 * pix + 2];
+    }
+    tfb[k] = T[k] * (bg.x * gr[k] + bg.y * gg[k] + bg.z * gb[k]);
+    mylast = max(mylast, last[k]);
   }
-  const float Tf = T;
-  const float bgdot = bg.x * gr + bg.y * gg + bg.z * gb;
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+  // positions >= the warp's largest n_last contribute to none of its pixels
+  int wlast = mylast;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  if (last > 0) atomicMax(&s_max, last);
+  if ((threadIdx.x & 31) == 0 && wlast > 0) atomicMax(&s_max, wlast);
   __syncthreads();
   const int maxlast = s_max;
-  const float fpx = (float)px, fpy = (float)py;
-  for (int b = maxlast; b > 0; b -= TILE_PIX) {
+  for (int b = maxlast; b > 0; b -= R_BATCH) {
     __syncthreads();
-    int k = b - 1 - (int)threadIdx.x;
-    if (k >= 0) {
-      uint32_t id = pvals[r.x + k];
-      s_id[threadIdx.x] = id;
-      s_xy[threadIdx.x] = xy[id];
-      s_co[threadIdx.x] = conic_o[id];
-      s_rgb[threadIdx.x] = rgb[id];
+    for (int t = threadIdx.x; t < R_BATCH; t += R_THREADS) {
+      int k = b - 1 - t;
+      if (k >= 0) {
+        uint32_t id = pvals[r.x + k];
+        float2 g = xy[id];
+        float4 co = conic_o[id];
+        float4 cc = rgb[id];
+        s_id[t] = id;
+        s_a[t] = make_float4(g.x, g.y, co.x, co.y);
+        s_b[t] = make_float4(co.z, co.w, cc.x, cc.y);
+        s_c[t] = cc.z;
+        s_h[t] = alpha_box(co.x, co.y, co.z, co.w);
+      }
     }
     __syncthreads();
-    const int m = min(TILE_PIX, b);
-    for (int j = 0; j < m; ++j) {
+    const int m = min(R_BATCH, b);
+    for (int j = max(0, b - wlast); j < m; ++j) {
       const int pos = b - 1 - j;
+      const float4 a = s_a[j];
+      if (warp_misses(q, a.x, a.y, s_h[j])) continue;
+      const float4 bb = s_b[j];
+      const float cb = s_c[j];
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
-      if (pos < last) {
-        float2 g = s_xy[j];
-        float4 co = s_co[j];
+#pragma unroll
+      for (int k = 0; k < R_PPT; ++k) {
         float dx, dy;
-        float power = splat_power(fpx, fpy, g.x, g.y, co.x, co.y, co.z, dx, dy);
+        const float power = splat_power(fpx, (float)(q.py0 + k), a.x, a.y, a.z, a.w, bb.x, dx, dy);
         float G;
-        float alpha = splat_alpha(co.w, power, G);
-        if (power <= 0.f && alpha >= ALPHA_MIN) {
-          contrib = true;
-          float oma = __fsub_rn(1.f, alpha);
-          float Ti = __fdiv_rn(T, oma);
-          float4 cc = s_rgb[j];
-          float w = alpha * Ti;
-          v[6] = w * gr;
-          v[7] = w * gg;
-          v[8] = w * gb;
-          float dal = Ti * (gr * (cc.x - S0) + gg * (cc.y - S1) + gb * (cc.z - S2)) - Tf * bgdot / oma;
-          S0 = alpha * cc.x + oma * S0;
-          S1 = alpha * cc.y + oma * S1;
-          S2 = alpha * cc.z + oma * S2;
-          T = Ti;
-          if (__fmul_rn(co.w, G) <= ALPHA_MAX) {
-            v[5] = G * dal;
-            float dpw = alpha * dal;
-            v[0] = dpw * (co.x * dx + co.y * dy);
-            v[1] = dpw * (co.y * dx + co.z * dy);
-            v[2] = -0.5f * dpw * dx * dx;
-            v[3] = -dpw * dx * dy;
-            v[4] = -0.5f * dpw * dy * dy;
-          }
-        }
+        const float alpha = splat_alpha(bb.y, power, G);
+        const bool ok = pos < last[k] && power <= 0.f && alpha >= ALPHA_MIN;
+        contrib |= ok;
+        const float al = ok ? alpha : 0.f;
+        const float oma = 1.f - al;
+        const float ioma = __frcp_rn(oma);
+        const float Ti = T[k] * ioma;
+        const float w = al * Ti;
+        v[6] += w * gr[k];
+        v[7] += w * gg[k];
+        v[8] += w * gb[k];
+        const float dal = Ti * (gr[k] * (bb.z - S0[k]) + gg[k] * (bb.w - S1[k]) + gb[k] * (cb - S2[k])) -
+                          tfb[k] * ioma;
+        S0[k] = al * bb.z + oma * S0[k];
+        S1[k] = al * bb.w + oma * S1[k];
+        S2[k] = al * cb + oma * S2[k];
+        T[k] = Ti;
+        const float dsel = (ok && __fmul_rn(bb.y, G) <= ALPHA_MAX) ? dal : 0.f;
+        v[5] += G * dsel;
+        const float dpw = al * dsel;
+        v[0] += dpw * (a.z * dx + a.w * dy);
+        v[1] += dpw * (a.w * dx + bb.x * dy);
+        v[2] += -0.5f * dpw * dx * dx;
+        v[3] += -dpw * dx * dy;
+        v[4] += -0.5f * dpw * dy * dy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) v[q] = warp_sum(v[q]);
+        for (int t = 0; t < 9; ++t) v[t] = warp_sum(v[t]);
         if ((threadIdx.x & 31) == 0) {
-          uint32_t id = s_id[j];
+          const uint32_t id = s_id[j];
 #pragma unroll
-          for (int q = 0; q < 9; ++q)
-            if (v[q] != 0.f) atomicAdd(&g2[(uint64_t)q * V + id], v[q]);
+          for (int t = 0; t < 9; ++t)
+            if (v[t] != 0.f) atomicAdd(&g2[(uint64_t)t * V + id], v[t]);
         }
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
-                                                              const uint32_t* __restrict__ ntiles,
-                                                              const float4* __restrict__ rgbv,
-                                                              const float4* __restrict__ conic_o,
-                                                              const float* __restrict__ g2, uint64_t V,
-                                                              float* __restrict__ grad, int grad_pool,
-                                                              unsigned cpi) {
-  const unsigned item = blockIdx.x / cpi;
-  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
-  const uint32_t B = rl.B;
-  if (lane >= B) return;
-  const uint64_t i = (uint64_t)item * B + lane;
-  if (lane >= rl.item_count[item] || ntiles[i] == 0) return;
-  const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
-  const float* p = rl.base + sbase;
-  float* out = grad_pool ? grad + sbase : grad + i;
-  const uint64_t ostride = grad_pool ? B : V;
-  const float gu = g2[i], gv = g2[V + i], gA = g2[2 * V + i], gB = g2[3 * V + i], gC = g2[4 * V + i];
-  const float gop = g2[5 * V + i];
-  const float gcol[3] = {g2[6 * V + i], g2[7 * V + i], g2[8 * V + i]};
+// Chain rule of the Level-2 preprocess (exact derivative of k_preprocess)
+// from the 2D gradients of one Gaussian (u, v, A, B, C, opacity, r, g, b) to
+// its 59 parameters, accumulated into g[] (kept in registers when unrolled).
+__device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restrict__ p, uint32_t B,
+                                           const float gv2[9], uint32_t clampbits, float opac, float gr[D]) {
+  const float gu = gv2[0], gv = gv2[1], gA = gv2[2], gB = gv2[3], gC = gv2[4];
+  const float gop = gv2[5];
+  const float gcol[3] = {gv2[6], gv2[7], gv2[8]};
   const float mx = p[0], my = p[B], mz = p[2 * B];
   float dmu[3] = {0.f, 0.f, 0.f};
   // ---- colour ----
@@ -454,7 +529,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
     sh_eval(d[0], d[1], d[2], Y);
     float Gs[16][3];
     sh_grad(d[0], d[1], d[2], Gs);
-    uint32_t cl = __float_as_uint(rgbv[i].w);
+    uint32_t cl = clampbits;
     float gc[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) gc[ch] = (cl >> ch) & 1u ? 0.f : gcol[ch];
@@ -464,7 +539,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         uint64_t f = 11 + 3 * kk + ch;
-        out[f * ostride] += Y[kk] * gc[ch];
+        gr[f] += Y[kk] * gc[ch];
         float shv = p[f * B];
         float w = gc[ch] * shv;
         dd[0] += w * Gs[kk][0];
@@ -478,8 +553,8 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   }
   // ---- opacity ----
   {
-    float op = conic_o[i].w;
-    out[10 * ostride] += gop * op * (1.f - op);
+    float op = opac;
+    gr[10] += gop * op * (1.f - op);
   }
   // ---- geometry ----
   KeyPath k = key_path(c, mx, my, mz);
@@ -534,9 +609,9 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   dt[2] += -gu * c.fx * k.tx / tz2 - gv * c.fy * k.ty / tz2;
 #pragma unroll
   for (int a = 0; a < 3; ++a) dmu[a] += c.R[a] * dt[0] + c.R[3 + a] * dt[1] + c.R[6 + a] * dt[2];
-  out[0] += dmu[0];
-  out[ostride] += dmu[1];
-  out[2 * ostride] += dmu[2];
+  gr[0] += dmu[0];
+  gr[1] += dmu[1];
+  gr[2] += dmu[2];
   // Sigma = M M^T, M = Rq diag(sc)
   float M[3][3];
 #pragma unroll
@@ -553,7 +628,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
       dsb += dM * g.Rq[a][b];
       dR[a][b] = dM * g.sc[b];
     }
-    out[(3 + b) * ostride] += dsb * g.sc[b];
+    gr[3 + b] += dsb * g.sc[b];
   }
   const float w = g.qw, x = g.qx, y = g.qy, z = g.qz;
   float gw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
@@ -565,10 +640,50 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
                     y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
   float qd = gw * w + gx * x + gy * y + gz * z;
   float iq = 1.f / g.qn;
-  out[6 * ostride] += (gw - w * qd) * iq;
-  out[7 * ostride] += (gx - x * qd) * iq;
-  out[8 * ostride] += (gy - y * qd) * iq;
-  out[9 * ostride] += (gz - z * qd) * iq;
+  gr[6] += (gw - w * qd) * iq;
+  gr[7] += (gx - x * qd) * iq;
+  gr[8] += (gy - y * qd) * iq;
+  gr[9] += (gz - z * qd) * iq;
+}
+
+// mode 0: store the gradient of every valid render-list position (zero for
+// Gaussians without a tile rect) into a local [59][V] array;
+// mode 1: add the gradient of visible Gaussians to that array;
+// mode 2: add into a pool with the render list's slot layout.
+__global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
+                                                              const uint32_t* __restrict__ ntiles,
+                                                              const float4* __restrict__ rgbv,
+                                                              const float4* __restrict__ conic_o,
+                                                              const float* __restrict__ g2, uint64_t V,
+                                                              float* __restrict__ grad, int mode, unsigned cpi) {
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  const uint32_t B = rl.B;
+  if (lane >= B) return;
+  const uint64_t i = (uint64_t)item * B + lane;
+  if (lane >= rl.item_count[item]) return;
+  const bool vis = ntiles[i] != 0;
+  if (!vis && mode != 0) return;
+  const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+  const float* p = rl.base + sbase;
+  float* out = mode == 2 ? grad + sbase : grad + i;
+  const uint64_t ostride = mode == 2 ? B : V;
+  float g[D];
+#pragma unroll
+  for (int f = 0; f < D; ++f) g[f] = 0.f;
+  if (vis) {
+    float gv2[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gv2[q] = g2[(uint64_t)q * V + i];
+    chain_rule(c, p, B, gv2, __float_as_uint(rgbv[i].w), conic_o[i].w, g);
+  }
+  if (mode == 0) {
+#pragma unroll
+    for (int f = 0; f < D; ++f) out[(uint64_t)f * ostride] = g[f];
+  } else {
+#pragma unroll
+    for (int f = 0; f < D; ++f) out[(uint64_t)f * ostride] += g[f];
+  }
 }
 
 __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
@@ -868,7 +983,7 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   }
   tm->end(StageTimer::SORT, s);
   tm->begin(StageTimer::FWD, s);
-  k_raster_fwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+  k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last);
   TGS_LAUNCHED();
   tm->end(StageTimer::FWD, s);
@@ -922,7 +1037,7 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
       TGS_LAUNCHED();
     }
   }
-  k_raster_fwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+  k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last);
   TGS_LAUNCHED();
 }
@@ -935,17 +1050,17 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
   TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * cs.cap_v * sizeof(float), s));
   if (cs.n_pairs == 0) return;
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
-  k_raster_bwd<<<(unsigned)tiles, TILE_PIX, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+  k_raster_bwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.cap_v);
   TGS_LAUNCHED();
 }
 
-void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad,
-                            bool grad_pool, cudaStream_t s) {
-  if (rl.capacity() == 0 || cs.n_vis == 0) return;
+void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
+                            cudaStream_t s) {
+  if (rl.capacity() == 0 || (cs.n_vis == 0 && mode != 0)) return;
   unsigned cpi = div_up(rl.B, PP_THREADS);
   k_preprocess_bwd<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v,
-                                                          grad, grad_pool ? 1 : 0, cpi);
+                                                          grad, mode, cpi);
   TGS_LAUNCHED();
 }
 

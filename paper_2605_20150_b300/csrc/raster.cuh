@@ -77,11 +77,12 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
 void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs,
                         const float* dl_dimage, cudaStream_t s);
 
-// Chain rule from cs.g2 to the 59 parameters.  Accumulates (+=) into
-// `grad`: either a local array [59][cap_v] (grad_pool == false) or a pool with
-// the render list's slot layout (grad_pool == true, grad = pool base).
-void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad,
-                            bool grad_pool, cudaStream_t s);
+// Chain rule from cs.g2 to the 59 parameters.  mode 0 stores every valid
+// position's gradient (zero when invisible) into a local [59][cap_v] array,
+// mode 1 adds visible gradients to it, mode 2 adds into a pool with the
+// render list's slot layout (grad = pool base).
+void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
+                            cudaStream_t s);
 
 // Masked Adam over the render list: rows with touched != 0 update params and
 // moments in the pool; `grad` is the local [59][cap_v] array; step counters per

@@ -418,14 +418,13 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     timer.begin(StageTimer::LOSS, comp);
     photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
     timer.end(StageTimer::LOSS, comp);
-    if (V) TGS_CUDA(cudaMemsetAsync(grad_local, 0, (uint64_t)D * V * sizeof(float), comp));
     for (uint32_t j = 0; j < J; ++j) {
       DevCam dc = make_devcam(p.cams[j]);
       timer.begin(StageTimer::BWD, comp);
       render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
       timer.end(StageTimer::BWD, comp);
       timer.begin(StageTimer::PBWD, comp);
-      render_backward_params(rl, dc, cams[j], grad_local, false, comp);
+      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp);
       timer.end(StageTimer::PBWD, comp);
     }
     timer.begin(StageTimer::ADAM, comp);
