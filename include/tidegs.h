@@ -131,6 +131,12 @@ tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, voi
 /* Waits for all queued work of the table. */
 tgs_status tgs_sync(tgs_table* t);
 
+/* Replaces all parameters (params_host: host, n x 59 in the original row
+ * order given to tgs_create), zeroes the Adam moments and step counters,
+ * empties the HBM cache and recomputes the block bounds.  The block order
+ * (Morton permutation) of the table is kept. */
+tgs_status tgs_set_params(tgs_table* t, const float* params_host);
+
 /* Flushes dirty resident blocks to the host tier (a consistency barrier,
  * Sec. 3.4) and writes the parameters in the caller's original row order.
  * out_host: host, n x 59. */

@@ -63,6 +63,7 @@ _SIGS = {
     "tgs_render": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_camera), _VP, _VP]),
     "tgs_sync": (ctypes.c_int32, [_VP]),
     "tgs_get_params": (ctypes.c_int32, [_VP, _VP]),
+    "tgs_set_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_state": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP]),
     "tgs_get_block_order": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_spheres": (ctypes.c_int32, [_VP, _VP]),
@@ -204,6 +205,12 @@ class TideTable:
 
     def sync(self):
         _check(load().tgs_sync(self.h))
+
+    def set_params(self, params):
+        """params: host numpy [n, 59] (original row order) or a CUDA tensor (copied to host)."""
+        if not isinstance(params, np.ndarray):
+            params = params.detach().cpu().numpy()
+        _check(load().tgs_set_params(self.h, _ptr(np.ascontiguousarray(params, np.float32))))
 
     def params(self):
         out = np.zeros((self.n, D), np.float32)

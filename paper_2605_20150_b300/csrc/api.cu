@@ -188,6 +188,13 @@ static void read_state(Table& T, float* params, float* m1, float* m2, bool origi
   }
 }
 
+tgs_status tgs_set_params(tgs_table* t, const float* params_host) {
+  return guard([&] {
+    TGS_CHECK(t, TGS_ERR_INVALID, "tgs_set_params: null table");
+    t->t.set_params(params_host);
+  });
+}
+
 tgs_status tgs_get_params(tgs_table* t, float* out_host) {
   return guard([&] {
     TGS_CHECK(t && out_host, TGS_ERR_INVALID, "tgs_get_params: null argument");

@@ -496,13 +496,34 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         v[4] += -0.5f * dpw * dy * dy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
+        // reduce-scatter of v[0..7] by recursive halving (lane l ends with the
+        // warp sum of value 4 bit4(l) + 2 bit3(l) + bit2(l)), v[8] by butterfly
+        const int l = threadIdx.x & 31;
+        const bool h4 = l & 16, h3 = l & 8, h2 = l & 4;
+        float b4[4];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) v[t] = warp_sum(v[t]);
-        if ((threadIdx.x & 31) == 0) {
-          const uint32_t id = s_id[j];
+        for (int t = 0; t < 4; ++t) {
+          const float keep = h4 ? v[4 + t] : v[t];
+          const float send = h4 ? v[t] : v[4 + t];
+          b4[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        float b2[2];
 #pragma unroll
-          for (int t = 0; t < 9; ++t)
-            if (v[t] != 0.f) atomicAdd(&g2[(uint64_t)t * V + id], v[t]);
+        for (int t = 0; t < 2; ++t) {
+          const float keep = h3 ? b4[2 + t] : b4[t];
+          const float send = h3 ? b4[t] : b4[2 + t];
+          b2[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        float b1 = (h2 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b2[0] : b2[1], 4);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
+        const float s8 = warp_sum(v[8]);
+        const uint32_t id = s_id[j];
+        if ((l & 3) == 0) {
+          const int q = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+          if (b1 != 0.f) atomicAdd(&g2[(uint64_t)q * V + id], b1);
+        } else if (l == 1 && s8 != 0.f) {
+          atomicAdd(&g2[8ull * V + id], s8);
         }
       }
     }

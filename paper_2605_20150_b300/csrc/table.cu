@@ -92,27 +92,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
 
   // ---- host tier: K block records [params | m | v], field-major inside
   TGS_CUDA(cudaHostAlloc((void**)&host, K * rec_floats * sizeof(float), cudaHostAllocPortable));
-  {
-    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (unsigned w = 0; w < nt; ++w)
-      th.emplace_back([&, w]() {
-        for (uint64_t k = w; k < K; k += nt) {
-          float* rec = host + k * rec_floats;
-          std::memset(rec + (uint64_t)D * B, 0, 2ull * D * B * sizeof(float));
-          for (uint32_t l = 0; l < B; ++l) {
-            uint64_t g = k * B + l;
-            if (g >= N) {
-              for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = 0.f;
-              continue;
-            }
-            const float* row = params + (uint64_t)perm[g] * D;
-            for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = row[f];
-          }
-        }
-      });
-    for (auto& t : th) t.join();
-  }
+  fill_host(params);
 
   // ---- device cache and state
   dalloc(pool, n_slots * rec_floats);
@@ -160,32 +140,78 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   dalloc(loss_dev, 4);
   TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
 
-  // ---- initial bounding spheres: stream the means and log-scales of every
-  // block through the first slots of the pool
-  {
-    uint64_t chunk = std::min<uint64_t>(n_slots, max_items);
-    for (uint64_t k0 = 0; k0 < K; k0 += chunk) {
-      uint64_t m = std::min(chunk, K - k0);
-      TGS_CUDA(cudaMemcpy2DAsync(pool, rec_floats * sizeof(float), host + k0 * rec_floats,
-                                 rec_floats * sizeof(float), 6ull * B * sizeof(float), m,
-                                 cudaMemcpyHostToDevice, comp));
-      for (uint64_t j = 0; j < m; ++j) {
-        uint64_t blk = k0 + j;
-        rl_host[j] = (uint32_t)j;
-        rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - blk * B);
-        rl_host[2ull * max_items + j] = (uint32_t)blk;
-      }
-      TGS_CUDA(cudaMemcpyAsync(rl_dev, rl_host, 3ull * max_items * sizeof(uint32_t), cudaMemcpyHostToDevice, comp));
-      block_bounds(render_list((uint32_t)m), nullptr, spheres, comp);
-      TGS_CUDA(cudaStreamSynchronize(comp));
-    }
-  }
+  init_spheres();
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
   dirty_host.assign(n_slots, 0);
   slot_free_ev.assign(n_slots, nullptr);
   slot_has_ev.assign(n_slots, 0);
   for (auto& e : slot_free_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  TGS_CUDA(cudaEventRecord(ev_comp, comp));
+  TGS_CUDA(cudaDeviceSynchronize());
+}
+
+// Host tier from caller rows (original order): block records with the
+// parameters of ids kB.. in Morton order and zero moments (lanes past n zero).
+void Table::fill_host(const float* params) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (unsigned w = 0; w < nt; ++w)
+    th.emplace_back([&, w]() {
+      for (uint64_t k = w; k < K; k += nt) {
+        float* rec = host + k * rec_floats;
+        std::memset(rec + (uint64_t)D * B, 0, 2ull * D * B * sizeof(float));
+        for (uint32_t l = 0; l < B; ++l) {
+          uint64_t g = k * B + l;
+          if (g >= N) {
+            for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = 0.f;
+            continue;
+          }
+          const float* row = params + (uint64_t)perm[g] * D;
+          for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = row[f];
+        }
+      }
+    });
+  for (auto& t : th) t.join();
+}
+
+// Bounding spheres of every block: means and log-scales of the host records
+// are streamed through the first slots of the pool.
+void Table::init_spheres() {
+  uint64_t chunk = std::min<uint64_t>(n_slots, max_items);
+  for (uint64_t k0 = 0; k0 < K; k0 += chunk) {
+    uint64_t m = std::min(chunk, K - k0);
+    TGS_CUDA(cudaMemcpy2DAsync(pool, rec_floats * sizeof(float), host + k0 * rec_floats, rec_floats * sizeof(float),
+                               6ull * B * sizeof(float), m, cudaMemcpyHostToDevice, comp));
+    for (uint64_t j = 0; j < m; ++j) {
+      uint64_t blk = k0 + j;
+      rl_host[j] = (uint32_t)j;
+      rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - blk * B);
+      rl_host[2ull * max_items + j] = (uint32_t)blk;
+    }
+    TGS_CUDA(cudaMemcpyAsync(rl_dev, rl_host, 3ull * max_items * sizeof(uint32_t), cudaMemcpyHostToDevice, comp));
+    block_bounds(render_list((uint32_t)m), nullptr, spheres, comp);
+    TGS_CUDA(cudaStreamSynchronize(comp));
+  }
+}
+
+// Replaces every parameter (rows in the caller's original order), zeroes the
+// moments and step counters and empties the cache.
+void Table::set_params(const float* params) {
+  TGS_CHECK(params, TGS_ERR_INVALID, "tgs_set_params: null params");
+  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  fill_host(params);
+  std::vector<uint32_t> a(K, 126u);
+  TGS_CUDA(cudaMemcpy(ages, a.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  TGS_CUDA(cudaMemset(block_step, 0, K * sizeof(uint32_t)));
+  TGS_CUDA(cudaMemset(dirty_dev, 0, n_slots));
+  for (uint32_t* b : {r_bits, r_next_bits, acc_bits, acc_next_bits}) TGS_CUDA(cudaMemset(b, 0, words * sizeof(uint32_t)));
+  slot_of.assign(K, -1);
+  block_of_slot.assign(n_slots, -1);
+  dirty_host.assign(n_slots, 0);
+  slot_has_ev.assign(n_slots, 0);
+  prep = Prepared();
+  init_spheres();
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
   TGS_CUDA(cudaDeviceSynchronize());
 }

@@ -86,6 +86,9 @@ struct Table {
 
   void create(const tgs_config& c, uint64_t n, const float* params_host);
   void destroy();
+  void fill_host(const float* params);
+  void init_spheres();
+  void set_params(const float* params);
   void prepare(const tgs_camera* cams, uint32_t J, Prepared& out);
   void issue_early(Prepared& p);
   void issue_evictions_and_late(Prepared& p);

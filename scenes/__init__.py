@@ -221,3 +221,140 @@ def camera_array(cam) -> np.ndarray:
     return np.concatenate([[cam["width"], cam["height"], cam["fx"], cam["fy"], cam["cx"], cam["cy"],
                             cam["znear"], cam["zfar"]], np.asarray(cam["R"]).reshape(9),
                            np.asarray(cam["t"]).reshape(3)]).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------
+# torch backend of the same streams (for scenes of 10^8 Gaussians, generated
+# on the GPU); bit-identical to the numpy functions above
+# ----------------------------------------------------------------------------
+def _t_lsr(z, k):
+    import torch
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _t_mix64(z):
+    m1 = int(np.int64(np.uint64(0xBF58476D1CE4E5B9).astype(np.int64)))
+    m2 = int(np.int64(np.uint64(0x94D049BB133111EB).astype(np.int64)))
+    z = (z ^ _t_lsr(z, 30)) * m1
+    z = (z ^ _t_lsr(z, 27)) * m2
+    return z ^ _t_lsr(z, 31)
+
+
+def t_u64(seed, stream, start, count, device):
+    """int64 tensor holding the bits of draws [start, start+count) of a stream."""
+    import torch
+    key = int(np.int64(stream_key(seed, stream).astype(np.int64)))
+    gamma = int(np.int64(GAMMA.astype(np.int64)))
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    return _t_mix64(idx * gamma + key)
+
+
+def t_uniform(seed, stream, count, lo=0.0, hi=1.0, start=0, device="cuda"):
+    import torch
+    x = _t_lsr(t_u64(seed, stream, start, count, device), 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * x
+
+
+def t_normal(seed, stream, count, mean=0.0, std=1.0, start=0, device="cuda"):
+    import torch
+    u = _t_lsr(t_u64(seed, stream, 2 * start, 2 * count, device), 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+    u1 = 1.0 - u[0::2]
+    u2 = u[1::2]
+    return mean + std * torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+
+
+def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_width=20.0, ground_frac=0.5,
+                 device="cuda", chunk=1 << 24):
+    """Synthetic street grid (world z up) of n Gaussians as a float32 torch
+    tensor [n, 59] on `device`: roads every 100 m over a side x side square,
+    a ground layer (ground_frac of the Gaussians, uniform over the square) and
+    building facades set back from the roads (heights U[10, 60] m per city
+    block, Gaussians uniform over the facade area).  Log-scales log(spacing/2)
+    + N(0, 0.3) with spacing the mean distance between neighbours; opacity
+    logit N(2, 0.5); SH DC from a smooth field plus a per-block tint, SH rest
+    N(0, 0.05).  Generated in chunks of `chunk` rows."""
+    import torch
+    nb = int(side // road_every)
+    heights = t_uniform(seed, 40, nb * nb, 10.0, 60.0, device=device)
+    tint = t_uniform(seed, 41, 3 * nb * nb, -0.15, 0.15, device=device).reshape(nb * nb, 3)
+    inner = road_every - road_width
+    facade_area = (4 * inner * heights).sum().item()
+    ground_area = side * side
+    n_ground = int(n * ground_frac)
+    n_fac = n - n_ground
+    spacing = math.sqrt((ground_area + facade_area) / n)
+    out = torch.empty((n, D), dtype=torch.float32, device=device)
+    # facade sampling: block by cumulative facade area
+    cdf = torch.cumsum(4 * inner * heights, 0)
+    cdf = cdf / cdf[-1]
+    for a in range(0, n, chunk):
+        m = min(chunk, n - a)
+        i = torch.arange(a, a + m, device=device)
+        u1 = t_uniform(seed, 42, m, start=a, device=device)
+        u2 = t_uniform(seed, 43, m, start=a, device=device)
+        u3 = t_uniform(seed, 44, m, start=a, device=device)
+        u4 = t_uniform(seed, 45, m, start=a, device=device)
+        pos = torch.empty((m, 3), dtype=torch.float64, device=device)
+        g = i < n_ground
+        pos[g, 0] = u1[g] * side - side / 2
+        pos[g, 1] = u2[g] * side - side / 2
+        pos[g, 2] = 0.0
+        f = ~g
+        blk = torch.searchsorted(cdf, u3[f].contiguous()).clamp_(max=nb * nb - 1)
+        bx = (blk // nb).to(torch.float64)
+        by = (blk % nb).to(torch.float64)
+        h = heights[blk]
+        side_id = (u4[f] * 4).floor().clamp_(max=3)
+        t = u1[f] * inner
+        x0 = bx * road_every - side / 2 + road_width / 2
+        y0 = by * road_every - side / 2 + road_width / 2
+        fx = torch.where(side_id == 0, x0 + t, torch.where(side_id == 1, x0 + t, torch.where(side_id == 2, x0, x0 + inner)))
+        fy = torch.where(side_id == 0, y0, torch.where(side_id == 1, y0 + inner, torch.where(side_id == 2, y0 + t, y0 + t)))
+        pos[f, 0] = fx
+        pos[f, 1] = fy
+        pos[f, 2] = u2[f] * h
+        row = out[a:a + m]
+        row[:, 0:3] = pos.to(torch.float32)
+        row[:, 3:6] = (math.log(0.5 * spacing) + t_normal(seed, 46, 3 * m, 0.0, 0.3, start=3 * a, device=device)
+                       ).reshape(m, 3).to(torch.float32)
+        q = t_normal(seed, 47, 4 * m, start=4 * a, device=device).reshape(m, 4)
+        row[:, 6:10] = (q / q.norm(dim=1, keepdim=True)).to(torch.float32)
+        row[:, 10] = t_normal(seed, 48, m, 2.0, 0.5, start=a, device=device).to(torch.float32)
+        rest = t_normal(seed, 49, 48 * m, 0.0, 0.05, start=48 * a, device=device).reshape(m, 16, 3)
+        cell = ((pos[:, 0] + side / 2) // road_every).clamp(0, nb - 1).long() * nb + \
+            ((pos[:, 1] + side / 2) // road_every).clamp(0, nb - 1).long()
+        col = torch.stack([0.5 + 0.25 * torch.sin(pos[:, 0] / 23.0 + 0.4 * c) * torch.cos(pos[:, 1] / 31.0 - 0.6 * c)
+                           + 0.1 * torch.sin(pos[:, 2] / 7.0 + c) for c in range(3)], 1) + tint[cell]
+        rest[:, 0, :] = (col - 0.5) * 3.5
+        row[:, 11:59] = rest.reshape(m, 48).to(torch.float32)
+        del pos, rest, col, q
+    return out, spacing
+
+
+def street_drive_cameras(n_cams=500, seed=1003, side=4000.0, road_every=100.0, height=1.5, step=2.0,
+                         width=1600, height_px=900, fov_x=90.0, znear=0.2, zfar=200.0, turn_every=400.0):
+    """A connected drive along the road centre lines: 2 m per frame at 1.5 m
+    height, turning left or right at an intersection every `turn_every`
+    metres (turn direction from the seeded stream), looking along the road."""
+    u = uniform(seed, 60, n_cams + 8)
+    pos = np.array([road_every * 3 - side / 2, road_every * 3 - side / 2])
+    d = np.array([1.0, 0.0])
+    travelled = 0.0
+    cams = []
+    k = 0
+    for i in range(n_cams):
+        p3 = np.array([pos[0], pos[1], height])
+        tgt = p3 + np.array([d[0], d[1], 0.0])
+        R, t = look_at(p3, tgt, up=(0.0, 0.0, 1.0))
+        cams.append(pinhole(width, height_px, fov_x, R, t, znear, zfar))
+        pos = pos + step * d
+        travelled += step
+        if travelled >= turn_every:
+            travelled = 0.0
+            left = u[k] < 0.5
+            k += 1
+            d = np.array([-d[1], d[0]]) if left else np.array([d[1], -d[0]])
+            nxt = pos + turn_every * d
+            if np.any(np.abs(nxt) > side / 2 - road_every):
+                d = -d
+    return cams
