@@ -1,6 +1,12 @@
 """Benchmark of the TideGS training step on B300 (train iterations per second).
 
-Workload (default): the fully resident FP32 aerial configuration -- 2,000,000
+Workload (default, --workload street100m): 100M Gaussians of a synthetic 4 km
+street grid in 4,096-Gaussian Morton blocks, FP32 parameters and Adam moments
+in pinned host memory, a 24 GB HBM working-set cache, 500 cameras at
+1600x900 along a street-level drive, batch 1, exact next-batch prefetch; the
+line carries the same-run host-link test and the streaming counters.
+
+--workload aerial2m: the fully resident FP32 aerial configuration -- 2,000,000
 Gaussians over a synthetic 1 km x 1 km block scene (jittered ground grid plus
 box buildings), 100 cameras on a circular orbit at 150 m altitude, 1920x1080,
 batch 1, one training step = cull + residency + Level-2 forward + L1 loss +
@@ -39,8 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=2_000_000)
-    ap.add_argument("--cams", type=int, default=100)
+    ap.add_argument("--workload", default="street100m", choices=["aerial2m", "street100m"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--cams", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -114,7 +121,7 @@ def measured_peaks():
 
 
 def build_workload(args):
-    cfg = scenes.aerial_config(n=args.n, n_cams=args.cams)
+    cfg = scenes.aerial_config(n=args.n or 2_000_000, n_cams=args.cams or 100)
     gt = cfg["params"]
     train = scenes.perturb(gt, seed=2001, mean_std=0.02 * cfg["spacing"])
     return cfg, gt, train
@@ -197,6 +204,159 @@ def run_ours(args, rank, world, local):
     e2e_ms = max(e2.elapsed_time(e3), 1e3 * wall_e2e) / n_e2e
     return dict(ms=ms, stages=stages, stats=st, launches=launches, clocks=clocks, rec=rec, table=table,
                 cfg=cfg, W=W, H=H, e2e_ms=e2e_ms, bytes_in=J * H * W * 3 * 4, train=train)
+
+
+def link_peak(torch, mb=256, reps=10):
+    """Same-run host-link test: pinned cudaMemcpyAsync of `mb` MB, best of
+    `reps`, H2D, D2H and both directions at once (GB/s)."""
+    n = mb * (1 << 20) // 4
+    h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    h2 = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(n, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = {}
+    for name in ("h2d", "d2h", "bidir"):
+        best = 0.0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name in ("h2d", "bidir"):
+                with torch.cuda.stream(s1):
+                    d.copy_(h, non_blocking=True)
+            if name in ("d2h", "bidir"):
+                with torch.cuda.stream(s2):
+                    h2.copy_(d2, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            nbytes = (2 if name == "bidir" else 1) * n * 4
+            best = max(best, nbytes / dt / 1e9)
+        out[name] = round(best, 2)
+    return out
+
+
+def run_street(args, rank, world, local):
+    """Out-of-core street workload: 100M Gaussians in 4,096-Gaussian Morton
+    blocks over a 4 km street grid, full FP32 state (params + 2 Adam moments,
+    708 B per Gaussian) in pinned host memory, HBM cache capped at 24 GB,
+    1600x900 cameras along a street-level drive at 1.5 m, batch 1, exact
+    next-batch prefetch.  Targets are renders of the unperturbed scene."""
+    import torch
+    import paper_2605_20150_b300 as tgs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n or 100_000_000
+    if world > 1:
+        # replicas share the host: keep N pinned host tiers within 60% of its memory
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        n = min(n, int(0.6 * avail / (world * 960)))
+    nc = args.cams or 500
+    t0 = time.perf_counter()
+    gt, spacing = scenes.street_scene(n, device=dev)
+    cams = scenes.street_drive_cameras(nc)
+    host = gt.cpu().numpy()
+    del gt
+    torch.cuda.empty_cache()
+    W, H = cams[0]["width"], cams[0]["height"]
+    cache = int(24e9 // (4096 * 708))
+    tcfg = dict(block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache, spare_slots=512,
+                prefetch_mode=1, moments_policy=0, loss=0)
+    table = tgs.TideTable(host, **tcfg)
+    t_create = time.perf_counter() - t0
+    targets = torch.empty(nc, H, W, 3, device=dev, dtype=torch.float32)
+    for i, c in enumerate(cams):
+        table.render(c, targets[i])
+    torch.cuda.synchronize()
+    chunk = 1 << 24
+    for a in range(0, n, chunk):
+        rows = torch.from_numpy(host[a:a + chunk]).to(dev)
+        scenes.t_perturb_(rows, 2003, a, mean_std=0.02 * spacing)
+        host[a:a + chunk] = rows.cpu().numpy()
+    table.set_params(host)
+    t_setup = time.perf_counter() - t0
+
+    def one(t):
+        table.step([cams[t % nc]], targets[t % nc:t % nc + 1], next_cams=[cams[(t + 1) % nc]], want_loss=False)
+
+    for t in range(args.warmup):
+        one(t)
+    table.sync()
+    st0 = table.stats()
+    table.stage_timing(True)
+    table.stage_ms(reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for t in range(args.warmup, args.warmup + args.steps):
+        one(t)
+    e1.record(s)
+    table.sync()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    stages = table.stage_ms(reset=True)
+    table.stage_timing(False)
+    st = table.stats()
+    delta = {k: st[k] - st0[k] for k in ("bytes_h2d", "bytes_d2h", "blocks_in", "blocks_out", "writebacks",
+                                         "readmissions", "stall_ms", "h2d_ms", "d2h_ms", "kernel_launches")}
+    rec = table.camera_record(0, W, H)
+    peak = link_peak(torch)
+    # end to end with host targets and the loss read back each step
+    host_t = torch.empty(min(nc, 64), H, W, 3, dtype=torch.float32, pin_memory=True)
+    host_t.copy_(targets[:host_t.shape[0]].cpu())
+    host_np = host_t.numpy()
+    n_e2e = max(5, args.steps // 2)
+    base = args.warmup + args.steps
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for t in range(n_e2e):
+        k = (base + t) % host_np.shape[0]
+        table.step([cams[(base + t) % nc]], host_np[k:k + 1], next_cams=[cams[(base + t + 1) % nc]], want_loss=True)
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
+    link = {"peak_gbs": peak, "bytes_h2d_per_step": delta["bytes_h2d"] / args.steps,
+            "bytes_d2h_per_step": delta["bytes_d2h"] / args.steps,
+            "h2d_gbs_while_copying": round(delta["bytes_h2d"] / max(delta["h2d_ms"], 1e-9) / 1e6, 2),
+            "d2h_gbs_while_copying": round(delta["bytes_d2h"] / max(delta["d2h_ms"], 1e-9) / 1e6, 2),
+            "h2d_frac_of_peak": round(delta["bytes_h2d"] / max(delta["h2d_ms"], 1e-9) / 1e6 / peak["h2d"], 4),
+            "stall_ms_per_step": round(delta["stall_ms"] / args.steps, 4),
+            "blocks_in_per_step": delta["blocks_in"] / args.steps, "blocks_out_per_step": delta["blocks_out"] / args.steps,
+            "writebacks": delta["writebacks"], "readmissions": delta["readmissions"]}
+    return dict(ms=ms, stages=stages, stats=st, launches=delta["kernel_launches"], clocks=clocks, rec=rec,
+                table=table, cams=cams, W=W, H=H, e2e_ms=e2e_ms, bytes_in=H * W * 3 * 4, link=link, n=n, nc=nc,
+                cache_blocks=cache, setup_s=round(t_setup, 1), create_s=round(t_create, 1), host=host)
+
+
+def cpu_baseline_street(res):
+    """The FP64 oracle on one full step of camera 0's neighbourhood: the input
+    rows within the camera's far distance (a superset of its visible set),
+    blocked, culled and trained at 1600x900."""
+    import oracle
+    oracle.build()
+    cam = res["cams"][0]
+    ca = scenes.camera_array(cam)
+    host = res["host"]
+    pos = -np.asarray(cam["R"]).T @ np.asarray(cam["t"])
+    sel = np.nonzero(np.sum((host[:, 0:3] - pos.astype(np.float32)) ** 2, axis=1) < cam["zfar"] ** 2)[0]
+    sub = host[sel]
+    B = 4096
+    perm, P = oracle.create(sub, B)
+    P = P.astype(np.float64)
+    sph = oracle.block_spheres(P, B)
+    _, vis = oracle.visible_blocks(sph, [ca])
+    blocks = np.nonzero(vis)[0]
+    target = np.zeros((1, int(ca[1]), int(ca[0]), 3))
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    steps = np.zeros(len(sph), np.int64)
+    t0 = time.perf_counter()
+    oracle.train_step(P, M1, M2, steps, B, blocks, [ca], target, lr=1e-3, loss_kind=0)
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 6), "unit": "train iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one step of camera 0: {len(sel)} Gaussians within {cam['zfar']:.0f} m, {len(blocks)} "
+                      f"visible blocks, 1600x900, FP64 forward+backward+Adam, {dt:.1f} s"}
 
 
 def roofline(res, steps):
@@ -298,16 +458,25 @@ def main():
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
-    res = run_ours(args, rank, world, local)
+    street = args.workload == "street100m"
+    res = run_street(args, rank, world, local) if street else run_ours(args, rank, world, local)
     ms_step = res["ms"] / args.steps
     value = world * 1e3 / ms_step
+    if street:
+        config = {"workload": "street-100M-1600x900-outofcore-fp32", "n_gaussians": res["n"], "block_size": 4096,
+                  "image": f"{res['W']}x{res['H']}", "global_batch": world, "cameras": res["nc"],
+                  "cache_blocks": res["cache_blocks"], "cache_gb": 24, "host_tier": "pinned FP32 params+m+v",
+                  "prefetch": "exact next batch", "parallelism": f"replicas{world}",
+                  "l2": "per-step state > 126 MB L2, no flush", "setup_s": res["setup_s"]}
+    else:
+        config = {"workload": "aerial-2M-1080p-resident-fp32", "n_gaussians": args.n or 2_000_000,
+                  "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
+                  "cameras": args.cams or 100, "parallelism": f"replicas{world}",
+                  "l2": "per-step state 1.4 GB > 126 MB L2, no flush"}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "train iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "aerial-2M-1080p-resident-fp32", "n_gaussians": args.n, "block_size": 4096,
-                   "image": f"{res['W']}x{res['H']}", "global_batch": world, "cameras": args.cams,
-                   "parallelism": f"replicas{world}", "l2": "per-step state 1.4 GB > 126 MB L2, no flush"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "e2e": {"value": round(world * 1e3 / res["e2e_ms"], 3), "unit": "train iters/s",
                 "h2d_bytes_per_step": res["bytes_in"], "d2h_bytes_per_step": 4},
         "gpu_launches": int(res["launches"]),
@@ -316,8 +485,10 @@ def main():
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["stages"].items()},
         "visible": res["stats"]["last_visible"], "pairs": res["stats"]["last_pairs"],
     }
+    if street:
+        line["link"] = res["link"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(res)
+        line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()
     if rank == 0:
         print(json.dumps(line))

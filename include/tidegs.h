@@ -177,13 +177,16 @@ tgs_status tgs_get_camera_record(tgs_table* t, uint32_t j, uint64_t* n_gauss, ui
                                  uint32_t* ranges, float* image, float* t_final, int32_t* n_last,
                                  float* grad2d);
 
-/* Counters (Tab. 4/5/9 style). */
+/* Counters (Tab. 4/5/9 style): steps, bytes and blocks moved each way,
+ * write-backs, re-admissions, cold restarts, kernel launches of the library,
+ * exposed copy time, copy-engine busy time, and the last render's sizes. */
 typedef struct tgs_stats {
   uint64_t steps;
   uint64_t bytes_h2d, bytes_d2h;
   uint64_t blocks_in, blocks_out, writebacks, readmissions, cold_restarts;
   uint64_t kernel_launches;
-  double stall_ms;
+  double stall_ms;          /* compute stream waiting for incoming blocks */
+  double h2d_ms, d2h_ms;    /* CUDA-event time of the copy batches on the copy streams */
   uint64_t last_pairs, last_visible, last_render_blocks;
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);

@@ -47,7 +47,8 @@ class tgs_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64),
                 ("blocks_in", ctypes.c_uint64), ("blocks_out", ctypes.c_uint64), ("writebacks", ctypes.c_uint64),
                 ("readmissions", ctypes.c_uint64), ("cold_restarts", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64), ("stall_ms", ctypes.c_double), ("last_pairs", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("stall_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
+                ("d2h_ms", ctypes.c_double), ("last_pairs", ctypes.c_uint64),
                 ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64)]
 
 

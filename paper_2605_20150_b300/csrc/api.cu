@@ -339,8 +339,11 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out) {
   return guard([&] {
     TGS_CHECK(t && out, TGS_ERR_INVALID, "tgs_get_stats: null argument");
     t->t.collect_stall();
+    t->t.copy_timer.collect();
     *out = t->t.stats;
     out->kernel_launches = g_launches;
+    out->h2d_ms = t->t.copy_timer.ms[0];
+    out->d2h_ms = t->t.copy_timer.ms[1];
   });
 }
 

@@ -69,6 +69,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
     TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   TGS_CUDA(cudaEventCreate(&ev_stall_a));
   TGS_CUDA(cudaEventCreate(&ev_stall_b));
+  copy_timer.on = true;
 
   // ---- Morton order on the device (Sec. 3.3): centres -> codes -> stable sort
   {
@@ -144,6 +145,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
   dirty_host.assign(n_slots, 0);
+  ever_loaded.assign(K, 0);
   slot_free_ev.assign(n_slots, nullptr);
   slot_has_ev.assign(n_slots, 0);
   for (auto& e : slot_free_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -210,6 +212,7 @@ void Table::set_params(const float* params) {
   block_of_slot.assign(n_slots, -1);
   dirty_host.assign(n_slots, 0);
   slot_has_ev.assign(n_slots, 0);
+  ever_loaded.assign(K, 0);
   prep = Prepared();
   init_spheres();
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
@@ -350,11 +353,18 @@ static void copy_block_in(Table& t, uint32_t b, uint32_t s, cudaStream_t st) {
   }
   t.dirty_host[s] = 0;
   t.stats.blocks_in++;
+  if (t.ever_loaded[b]) t.stats.readmissions++;
+  t.ever_loaded[b] = 1;
 }
 
 void Table::issue_early(Prepared& p) {
   if (!cfg.overlap) TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
-  for (size_t i = 0; i < p.plan.early_block.size(); ++i) copy_block_in(*this, p.plan.early_block[i], p.plan.early_slot[i], h2d);
+  if (!p.plan.early_block.empty()) {
+    copy_timer.begin(0, h2d);
+    for (size_t i = 0; i < p.plan.early_block.size(); ++i)
+      copy_block_in(*this, p.plan.early_block[i], p.plan.early_slot[i], h2d);
+    copy_timer.end(0, h2d);
+  }
   TGS_CUDA(cudaEventRecord(ev_h2d, h2d));
 }
 
@@ -363,6 +373,10 @@ void Table::issue_early(Prepared& p) {
 void Table::issue_evictions_and_late(Prepared& p) {
   TGS_CUDA(cudaStreamWaitEvent(d2h, ev_comp, 0));
   const uint64_t pf = (uint64_t)D * B;
+  bool any_wb = false;
+  for (size_t i = 0; i < p.plan.evict_block.size(); ++i)
+    if (dirty_host[p.plan.evict_slot[i]]) any_wb = true;
+  if (any_wb) copy_timer.begin(1, d2h);
   for (size_t i = 0; i < p.plan.evict_block.size(); ++i) {
     uint32_t b = p.plan.evict_block[i], s = p.plan.evict_slot[i];
     if (dirty_host[s]) {
@@ -377,8 +391,14 @@ void Table::issue_evictions_and_late(Prepared& p) {
     slot_has_ev[s] = 1;
     stats.blocks_out++;
   }
+  if (any_wb) copy_timer.end(1, d2h);
   TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
-  for (size_t i = 0; i < p.plan.late_block.size(); ++i) copy_block_in(*this, p.plan.late_block[i], p.plan.late_slot[i], h2d);
+  if (!p.plan.late_block.empty()) {
+    copy_timer.begin(0, h2d);
+    for (size_t i = 0; i < p.plan.late_block.size(); ++i)
+      copy_block_in(*this, p.plan.late_block[i], p.plan.late_slot[i], h2d);
+    copy_timer.end(0, h2d);
+  }
   TGS_CUDA(cudaEventRecord(ev_h2d, h2d));
 }
 

@@ -68,6 +68,7 @@ struct Table {
   std::vector<uint8_t> dirty_host;       // n_slots
   std::vector<cudaEvent_t> slot_free_ev; // n_slots (null = no pending use)
   std::vector<uint8_t> slot_has_ev;
+  std::vector<uint8_t> ever_loaded;      // K: for the re-admission counter
 
   // last computed batch (for the debug getters)
   std::vector<tgs_camera> last_cams;
@@ -83,6 +84,7 @@ struct Table {
 
   tgs_stats stats{};
   StageTimer timer;
+  StageTimer copy_timer;  // stage 0: H2D batches, stage 1: D2H batches (always on)
 
   void create(const tgs_config& c, uint64_t n, const float* params_host);
   void destroy();

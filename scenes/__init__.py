@@ -358,3 +358,15 @@ def street_drive_cameras(n_cams=500, seed=1003, side=4000.0, road_every=100.0, h
             if np.any(np.abs(nxt) > side / 2 - road_every):
                 d = -d
     return cams
+
+
+def t_perturb_(rows, seed, row0, mean_std=0.02, logscale_std=0.1, opacity_std=0.5, sh_std=0.05):
+    """In-place torch version of perturb() on rows [row0, row0 + len(rows)) of a
+    table (same streams and indices, so chunks compose to the whole table)."""
+    m = rows.shape[0]
+    dev = rows.device
+    rows[:, 0:3] += t_normal(seed, 11, 3 * m, 0.0, mean_std, start=3 * row0, device=dev).reshape(m, 3).to(rows.dtype)
+    rows[:, 3:6] += t_normal(seed, 12, 3 * m, 0.0, logscale_std, start=3 * row0, device=dev).reshape(m, 3).to(rows.dtype)
+    rows[:, 10] += t_normal(seed, 13, m, 0.0, opacity_std, start=row0, device=dev).to(rows.dtype)
+    rows[:, 11:59] += t_normal(seed, 14, 48 * m, 0.0, sh_std, start=48 * row0, device=dev).reshape(m, 48).to(rows.dtype)
+    return rows
