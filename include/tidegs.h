@@ -82,8 +82,13 @@ typedef struct tgs_config {
   float cull_margin_px;    /* Level-1 side-plane margin in pixels */
   float bg[3];             /* background colour */
   uint32_t loss;           /* 0: L1 mean, 1: L2 mean (photometric loss f_i, App. A.1) */
-  uint32_t host_bf16;      /* 1: SH-rest coefficients and Adam moments are BF16 in the
-                              host tier and the cache (not the paper's; FP32 = 0) */
+  uint32_t host_bf16;      /* 1: the 45 SH-rest coefficients and both Adam moments are
+                              BF16 in the host tier and the cache (382 instead of 708
+                              bytes per Gaussian; not in the paper); projection, blending
+                              and accumulation stay FP32.  Needs an even block_size. */
+  uint32_t stochastic_round; /* BF16 stores of Adam: 1 stochastic rounding (counter hash
+                              of seed, Gaussian id, field, step), 0 round to nearest */
+  uint32_t seed;
 } tgs_config;
 
 void tgs_default_config(tgs_config* cfg);

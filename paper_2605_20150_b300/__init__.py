@@ -40,7 +40,7 @@ class tgs_config(ctypes.Structure):
                 ("max_height", ctypes.c_uint32), ("quota", ctypes.c_uint32), ("lambda_", ctypes.c_float),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("cull_margin_px", ctypes.c_float), ("bg", ctypes.c_float * 3), ("loss", ctypes.c_uint32),
-                ("host_bf16", ctypes.c_uint32)]
+                ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32)]
 
 
 class tgs_stats(ctypes.Structure):

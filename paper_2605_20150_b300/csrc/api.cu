@@ -1,5 +1,7 @@
 // extern "C" boundary of the library (declared in include/tidegs.h).  Every
 // entry point converts exceptions into a status and a thread-local message.
+#include <cuda_bf16.h>
+
 #include <cstring>
 #include <string>
 #include <vector>
@@ -112,6 +114,8 @@ void tgs_default_config(tgs_config* c) {
   c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
   c->loss = 0;
   c->host_bf16 = 0;
+  c->stochastic_round = 1;
+  c->seed = 1234;
 }
 
 tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_host, tgs_table** out) {
@@ -164,6 +168,7 @@ tgs_status tgs_sync(tgs_table* t) {
 static void read_state(Table& T, float* params, float* m1, float* m2, bool original_order) {
   T.flush();
   const uint64_t B = T.B, rf = T.rec_floats;
+  const bool bf = T.cfg.host_bf16 != 0;
   // moments of resident blocks under cold restart live only in the cache
   std::vector<float> resident;
   std::vector<int64_t> slot_of = T.slot_of;
@@ -171,19 +176,27 @@ static void read_state(Table& T, float* params, float* m1, float* m2, bool origi
     resident.resize(T.n_slots * rf);
     TGS_CUDA(cudaMemcpy(resident.data(), T.pool, T.n_slots * rf * sizeof(float), cudaMemcpyDeviceToHost));
   }
+  auto moment = [&](const float* rec, int q, int f, uint64_t l) -> float {
+    const float* base = rec + T.p_floats + (uint64_t)q * T.m_floats;
+    if (bf) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[(uint64_t)f * B + l]);
+    return base[(uint64_t)f * B + l];
+  };
   for (uint64_t g = 0; g < T.N; ++g) {
     uint64_t k = g / B, l = g % B;
     const float* rec = T.host + k * rf;
     uint64_t row = original_order ? T.perm[g] : g;
     if (params)
-      for (int f = 0; f < D; ++f) params[row * D + f] = rec[(uint64_t)f * B + l];
+      for (int f = 0; f < D; ++f)
+        params[row * D + f] =
+            (bf && f >= F_BF16)
+                ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rec + (uint64_t)F_BF16 * B)[(uint64_t)(f - F_BF16) * B + l])
+                : rec[(uint64_t)f * B + l];
     const float* mrec = rec;
     if (T.cfg.moments_policy == 1) mrec = slot_of[k] >= 0 ? resident.data() + (uint64_t)slot_of[k] * rf : nullptr;
     for (int q = 0; q < 2; ++q) {
       float* dst = q == 0 ? m1 : m2;
       if (!dst) continue;
-      for (int f = 0; f < D; ++f)
-        dst[row * D + f] = mrec ? mrec[(uint64_t)(q + 1) * D * B + (uint64_t)f * B + l] : 0.f;
+      for (int f = 0; f < D; ++f) dst[row * D + f] = mrec ? moment(mrec, q, f, l) : 0.f;
     }
   }
 }

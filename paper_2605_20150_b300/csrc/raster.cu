@@ -29,6 +29,37 @@ namespace {
 
 constexpr int PP_THREADS = 256;
 
+// Parameter field f of one Gaussian: FP32 storage, or (BF16 form) BF16 for
+// the SH-rest coefficients f >= 14.
+template <bool BF>
+__device__ __forceinline__ float ldp(const float* __restrict__ p32, const __nv_bfloat16* __restrict__ p16, uint32_t B,
+                                     int f) {
+  if (BF && f >= F_BF16) return __bfloat162float(p16[(uint64_t)(f - F_BF16) * B]);
+  return p32[(uint64_t)f * B];
+}
+
+__device__ __forceinline__ const __nv_bfloat16* sh16(const float* slot_lane0, uint32_t B, uint32_t lane) {
+  return reinterpret_cast<const __nv_bfloat16*>(slot_lane0 + (uint64_t)F_BF16 * B) + lane;
+}
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) as a counter hash.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// FP32 -> BF16: round to nearest even, or stochastically (add 16 random bits
+// below the kept mantissa, then truncate; unbiased in expectation).
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x, bool sr, uint64_t key) {
+  if (!sr) return __float2bfloat16_rn(x);
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7F800000u) == 0x7F800000u) return __float2bfloat16_rn(x);
+  uint32_t r = (uint32_t)(mix64(key) & 0xFFFFu);
+  uint32_t v = (u + r) & 0xFFFF0000u;
+  return __ushort_as_bfloat16((unsigned short)(v >> 16));
+}
+
 // Real SH normalisations (sqrt(2) Re/Im of the Condon-Shortley complex
 // harmonics, l <= 3), from their closed forms:
 constexpr float K00 = 0.28209479177387814f;  // 1/(2 sqrt(pi))
@@ -158,6 +189,7 @@ struct PPOut {
   uint32_t* vflag;
 };
 
+template <bool BF>
 __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam c, PPOut o, uint8_t* touched,
                                                           uint32_t* item_touched, unsigned cpi) {
   const unsigned item = blockIdx.x / cpi;
@@ -167,7 +199,9 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
   const uint64_t i = (uint64_t)item * B + lane;
   uint32_t area = 0;
   if (lane < rl.item_count[item]) {
-    const float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+    const float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+    const float* p = slot + lane;
+    const __nv_bfloat16* q16 = sh16(slot, B, lane);
     float mx = p[0], my = p[B], mz = p[2 * B];
     KeyPath k = key_path(c, mx, my, mz);
     if (k.tz > c.znear && k.tz <= c.zfar) {
@@ -192,7 +226,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
 #pragma unroll
           for (int kk = 0; kk < 16; ++kk)
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) col[ch] += Y[kk] * p[(uint64_t)(11 + 3 * kk + ch) * B];
+            for (int ch = 0; ch < 3; ++ch) col[ch] += Y[kk] * ldp<BF>(p, q16, B, 11 + 3 * kk + ch);
           uint32_t clampbits = (col[0] < 0.f ? 1u : 0u) | (col[1] < 0.f ? 2u : 0u) | (col[2] < 0.f ? 4u : 0u);
           float opac = 1.f / (1.f + expf(-p[10 * B]));
           o.xy[i] = make_float2(k.u, k.v);
@@ -533,7 +567,9 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
 // Chain rule of the Level-2 preprocess (exact derivative of k_preprocess)
 // from the 2D gradients of one Gaussian (u, v, A, B, C, opacity, r, g, b) to
 // its 59 parameters, accumulated into g[] (kept in registers when unrolled).
-__device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restrict__ p, uint32_t B,
+template <bool BF>
+__device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restrict__ p,
+                                           const __nv_bfloat16* __restrict__ q16, uint32_t B,
                                            const float gv2[9], uint32_t clampbits, float opac, float gr[D]) {
   const float gu = gv2[0], gv = gv2[1], gA = gv2[2], gB = gv2[3], gC = gv2[4];
   const float gop = gv2[5];
@@ -561,7 +597,7 @@ __device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restr
       for (int ch = 0; ch < 3; ++ch) {
         uint64_t f = 11 + 3 * kk + ch;
         gr[f] += Y[kk] * gc[ch];
-        float shv = p[f * B];
+        float shv = ldp<BF>(p, q16, B, (int)f);
         float w = gc[ch] * shv;
         dd[0] += w * Gs[kk][0];
         dd[1] += w * Gs[kk][1];
@@ -671,12 +707,14 @@ __device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restr
 // Gaussians without a tile rect) into a local [59][V] array;
 // mode 1: add the gradient of visible Gaussians to that array;
 // mode 2: add into a pool with the render list's slot layout.
+template <bool BF>
 __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
                                                               const uint32_t* __restrict__ ntiles,
                                                               const float4* __restrict__ rgbv,
                                                               const float4* __restrict__ conic_o,
                                                               const float* __restrict__ g2, uint64_t V,
-                                                              float* __restrict__ grad, int mode, unsigned cpi) {
+                                                              float* __restrict__ grad, uint64_t Vg, int mode,
+                                                              unsigned cpi) {
   const unsigned item = blockIdx.x / cpi;
   const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
   const uint32_t B = rl.B;
@@ -687,8 +725,9 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   if (!vis && mode != 0) return;
   const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
   const float* p = rl.base + sbase;
+  const __nv_bfloat16* q16 = sh16(rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride, B, lane);
   float* out = mode == 2 ? grad + sbase : grad + i;
-  const uint64_t ostride = mode == 2 ? B : V;
+  const uint64_t ostride = mode == 2 ? B : Vg;
   float g[D];
 #pragma unroll
   for (int f = 0; f < D; ++f) g[f] = 0.f;
@@ -696,7 +735,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
     float gv2[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) gv2[q] = g2[(uint64_t)q * V + i];
-    chain_rule(c, p, B, gv2, __float_as_uint(rgbv[i].w), conic_o[i].w, g);
+    chain_rule<BF>(c, p, q16, B, gv2, __float_as_uint(rgbv[i].w), conic_o[i].w, g);
   }
   if (mode == 0) {
 #pragma unroll
@@ -707,6 +746,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   }
 }
 
+template <bool BF>
 __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
                                                     const uint8_t* __restrict__ touched,
                                                     const uint32_t* __restrict__ block_step, uint64_t V, float lr,
@@ -717,21 +757,50 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
   if (lane >= B) return;
   const uint64_t i = (uint64_t)item * B + lane;
   if (lane >= rl.item_count[item] || !touched[i]) return;
-  const float tau = (float)block_step[rl.item_block[item]];
+  const uint32_t blk = rl.item_block[item];
+  const uint32_t step = block_step[blk];
+  const float tau = (float)step;
   const float c1 = 1.f - powf(b1, tau), c2 = 1.f - powf(b2, tau);
   const float ic1 = 1.f / c1, ic2 = 1.f / c2;
-  float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
-  float* m = p + rl.m_off;
-  float* v = p + rl.v_off;
+  float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+  float* p = slot + lane;
+  if (!BF) {
+    float* m = p + rl.m_off;
+    float* v = p + rl.v_off;
 #pragma unroll 4
-  for (int f = 0; f < D; ++f) {
-    const uint64_t o = (uint64_t)f * B;
-    float gf = grad[(uint64_t)f * V + i];
-    float mf = b1 * m[o] + (1.f - b1) * gf;
-    float vf = b2 * v[o] + (1.f - b2) * gf * gf;
-    m[o] = mf;
-    v[o] = vf;
-    p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+    for (int f = 0; f < D; ++f) {
+      const uint64_t o = (uint64_t)f * B;
+      float gf = grad[(uint64_t)f * V + i];
+      float mf = b1 * m[o] + (1.f - b1) * gf;
+      float vf = b2 * v[o] + (1.f - b2) * gf * gf;
+      m[o] = mf;
+      v[o] = vf;
+      p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+    }
+  } else {
+    __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
+    __nv_bfloat16* m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
+    __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
+    const bool sr = rl.sr != 0;
+    const uint64_t gid = (uint64_t)blk * B + lane;
+    const uint64_t key0 = ((uint64_t)rl.seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20);
+#pragma unroll 4
+    for (int f = 0; f < D; ++f) {
+      const uint64_t o = (uint64_t)f * B;
+      float gf = grad[(uint64_t)f * V + i];
+      float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
+      float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
+      const float upd = lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+      const uint64_t key = key0 + (uint64_t)f * 4;
+      m[o] = to_bf16(mf, sr, key);
+      v[o] = to_bf16(vf, sr, key + 1);
+      if (f < F_BF16) {
+        p[o] -= upd;
+      } else {
+        const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
+        q[o16] = to_bf16(__bfloat162float(q[o16]) - upd, sr, key + 2);
+      }
+    }
   }
 }
 
@@ -971,7 +1040,10 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
     unsigned cpi = div_up(rl.B, PP_THREADS);
     PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
     tm->begin(StageTimer::PRE, s);
-    k_preprocess<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
+    if (rl.bf16)
+      k_preprocess<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
+    else
+      k_preprocess<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
     TGS_LAUNCHED();
     tm->end(StageTimer::PRE, s);
     tm->begin(StageTimer::SORT, s);
@@ -1029,7 +1101,7 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
   if (V > 0) {
     unsigned cpi = div_up(rl.B, PP_THREADS);
     PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
-    k_preprocess<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, nullptr, nullptr, cpi);
+    k_preprocess<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, nullptr, nullptr, cpi);
     TGS_LAUNCHED();
     exclusive_scan_u32(cs.scan, cs.scan, cs.counters, V, cs.scratch, s);
     k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
@@ -1080,8 +1152,12 @@ void render_backward_params(const RenderList& rl, const DevCam& cam, const CamSt
                             cudaStream_t s) {
   if (rl.capacity() == 0 || (cs.n_vis == 0 && mode != 0)) return;
   unsigned cpi = div_up(rl.B, PP_THREADS);
-  k_preprocess_bwd<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v,
-                                                          grad, mode, cpi);
+  if (rl.bf16)
+    k_preprocess_bwd<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
+                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi);
+  else
+    k_preprocess_bwd<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
+                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi);
   TGS_LAUNCHED();
 }
 
@@ -1089,7 +1165,12 @@ void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* to
                       float lr, float b1, float b2, float eps, cudaStream_t s) {
   if (rl.capacity() == 0) return;
   unsigned cpi = div_up(rl.B, PP_THREADS);
-  k_adam<<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2, eps, cpi);
+  if (rl.bf16)
+    k_adam<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2, eps,
+                                                        cpi);
+  else
+    k_adam<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2,
+                                                         eps, cpi);
   TGS_LAUNCHED();
 }
 

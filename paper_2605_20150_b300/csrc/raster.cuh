@@ -2,6 +2,8 @@
 // tile binning, depth sort, front-to-back compositing and their backward,
 // run over the Gaussians of a render list of resident blocks.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "stage_timer.cuh"
 
@@ -12,6 +14,13 @@ namespace tgs {
 // apart; inside a slot, field f of lane l is at f * B + l (params), and at
 // m_off + f * B + l / v_off + f * B + l for the Adam moments when present.
 // Render-list position of lane l of item j: j * B + l.
+// BF16 form (bf16 != 0): fields 0..13 (mean, log-scale, quaternion,
+// opacity, SH DC) stay FP32 at f * B + l; the 45 SH-rest coefficients are
+// BF16 at (bf16*)(slot + 14 B) + (f - 14) * B + l; both moments are BF16 at
+// (bf16*)(slot + m_off / v_off) + f * B + l.  Adam's BF16 stores round
+// stochastically (sr != 0, counter hash of seed, Gaussian id, field, step) or
+// to nearest.
+constexpr int F_BF16 = 14;
 struct RenderList {
   float* base;
   uint64_t slot_stride;
@@ -21,6 +30,7 @@ struct RenderList {
   const uint32_t* item_count;  // device [n_items], Gaussians in the block
   const uint32_t* item_block;  // device [n_items], block id
   uint64_t m_off, v_off;       // moment offsets inside a slot (floats)
+  uint32_t bf16 = 0, sr = 0, seed = 0;
   uint64_t capacity() const { return (uint64_t)n_items * B; }
 };
 
@@ -78,14 +88,14 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
                         const float* dl_dimage, cudaStream_t s);
 
 // Chain rule from cs.g2 to the 59 parameters.  mode 0 stores every valid
-// position's gradient (zero when invisible) into a local [59][cap_v] array,
+// position's gradient (zero when invisible) into a local [59][rl.capacity()] array,
 // mode 1 adds visible gradients to it, mode 2 adds into a pool with the
 // render list's slot layout (grad = pool base).
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
                             cudaStream_t s);
 
 // Masked Adam over the render list: rows with touched != 0 update params and
-// moments in the pool; `grad` is the local [59][cap_v] array; step counters per
+// moments in the pool; `grad` is the local [59][rl.capacity()] array; step counters per
 // block id (already incremented for this step).
 void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const uint32_t* block_step,
                       float lr, float b1, float b2, float eps, cudaStream_t s);

@@ -11,6 +11,8 @@
 #include <cstring>
 #include <thread>
 
+#include <cuda_bf16.h>
+
 #include "sort.cuh"
 #include "table.cuh"
 
@@ -38,8 +40,11 @@ RenderList Table::render_list(uint32_t n_items) const {
   rl.item_slot = rl_dev;
   rl.item_count = rl_dev + max_items;
   rl.item_block = rl_dev + 2 * (uint64_t)max_items;
-  rl.m_off = (uint64_t)D * B;
-  rl.v_off = 2ull * D * B;
+  rl.m_off = p_floats;
+  rl.v_off = p_floats + m_floats;
+  rl.bf16 = cfg.host_bf16 ? 1u : 0u;
+  rl.sr = cfg.stochastic_round ? 1u : 0u;
+  rl.seed = cfg.seed;
   return rl;
 }
 
@@ -49,7 +54,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CHECK(c.block_size >= 1 && c.block_size <= 65536, TGS_ERR_INVALID, "block_size out of range [1, 65536]");
   TGS_CHECK(c.max_batch >= 1 && c.max_width >= 1 && c.max_height >= 1, TGS_ERR_INVALID, "bad batch/image limits");
   TGS_CHECK(n < (1ull << 32), TGS_ERR_INVALID, "n must be below 2^32");
-  TGS_CHECK(c.host_bf16 == 0, TGS_ERR_INVALID, "host_bf16 is not available in this build");
+  TGS_CHECK(c.host_bf16 == 0 || c.block_size % 2 == 0, TGS_ERR_INVALID, "host_bf16 needs an even block_size");
   N = n;
   B = c.block_size;
   K = (N + B - 1) / B;
@@ -57,7 +62,16 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   C = c.cache_blocks == 0 || c.cache_blocks > K ? K : c.cache_blocks;
   n_slots = C + (C < K ? c.spare_slots : 0);
   if (n_slots > K) n_slots = K;
-  rec_floats = 3ull * D * B;
+  // FP32 record: params 59 B + m 59 B + v 59 B floats (708 bytes per Gaussian).
+  // BF16 record: 14 FP32 fields + 45 BF16 SH-rest + BF16 m and v (382 bytes).
+  if (c.host_bf16) {
+    p_floats = (uint64_t)(F_BF16 * 4 + (D - F_BF16) * 2) * B / 4;
+    m_floats = (uint64_t)D * 2 * B / 4;
+  } else {
+    p_floats = (uint64_t)D * B;
+    m_floats = (uint64_t)D * B;
+  }
+  rec_floats = p_floats + 2 * m_floats;
   max_items = (uint32_t)C;
   V_cap = (uint64_t)max_items * B;
 
@@ -65,7 +79,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&ctl, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user})
+  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb})
     TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   TGS_CUDA(cudaEventCreate(&ev_stall_a));
   TGS_CUDA(cudaEventCreate(&ev_stall_b));
@@ -146,6 +160,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   block_of_slot.assign(n_slots, -1);
   dirty_host.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
+  wb_pending.assign(K, 0);
   slot_free_ev.assign(n_slots, nullptr);
   slot_has_ev.assign(n_slots, 0);
   for (auto& e : slot_free_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -158,19 +173,23 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
 void Table::fill_host(const float* params) {
   unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   std::vector<std::thread> th;
+  const bool bf = cfg.host_bf16 != 0;
   for (unsigned w = 0; w < nt; ++w)
     th.emplace_back([&, w]() {
       for (uint64_t k = w; k < K; k += nt) {
         float* rec = host + k * rec_floats;
-        std::memset(rec + (uint64_t)D * B, 0, 2ull * D * B * sizeof(float));
+        __nv_bfloat16* rec16 = reinterpret_cast<__nv_bfloat16*>(rec + (uint64_t)F_BF16 * B);
+        std::memset(rec + p_floats, 0, 2 * m_floats * sizeof(float));
         for (uint32_t l = 0; l < B; ++l) {
           uint64_t g = k * B + l;
-          if (g >= N) {
-            for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = 0.f;
-            continue;
+          const float* row = g < N ? params + (uint64_t)perm[g] * D : nullptr;
+          for (int f = 0; f < D; ++f) {
+            float x = row ? row[f] : 0.f;
+            if (bf && f >= F_BF16)
+              rec16[(uint64_t)(f - F_BF16) * B + l] = __float2bfloat16_rn(x);
+            else
+              rec[(uint64_t)f * B + l] = x;
           }
-          const float* row = params + (uint64_t)perm[g] * D;
-          for (int f = 0; f < D; ++f) rec[(uint64_t)f * B + l] = row[f];
         }
       }
     });
@@ -213,6 +232,7 @@ void Table::set_params(const float* params) {
   dirty_host.assign(n_slots, 0);
   slot_has_ev.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
+  wb_pending.assign(K, 0);
   prep = Prepared();
   init_spheres();
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
@@ -235,7 +255,7 @@ void Table::destroy() {
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b})
+  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb})
     if (e) cudaEventDestroy(e);
   for (cudaStream_t s : {comp, h2d, d2h, ctl})
     if (s) cudaStreamDestroy(s);
@@ -337,13 +357,19 @@ void Table::prepare(const tgs_camera* cs, uint32_t J, Prepared& out) {
 }
 
 static void copy_block_in(Table& t, uint32_t b, uint32_t s, cudaStream_t st) {
-  const uint64_t pf = (uint64_t)D * t.B;
+  const uint64_t pf = t.p_floats;
   float* dst = t.pool + (uint64_t)s * t.rec_floats;
   const float* src = t.host + (uint64_t)b * t.rec_floats;
   if (t.slot_has_ev[s]) TGS_CUDA(cudaStreamWaitEvent(st, t.slot_free_ev[s], 0));
+  // a block evicted earlier may still be on its way back to the host tier:
+  // wait for the latest write-back batch (it includes this block's)
+  if (t.wb_pending[b]) {
+    TGS_CUDA(cudaStreamWaitEvent(st, t.ev_wb, 0));
+    t.wb_pending[b] = 0;
+  }
   if (t.cfg.moments_policy == 1) {
     TGS_CUDA(cudaMemcpyAsync(dst, src, pf * sizeof(float), cudaMemcpyHostToDevice, st));
-    TGS_CUDA(cudaMemsetAsync(dst + pf, 0, 2 * pf * sizeof(float), st));
+    TGS_CUDA(cudaMemsetAsync(dst + pf, 0, 2 * t.m_floats * sizeof(float), st));
     TGS_CUDA(cudaMemsetAsync(t.block_step + b, 0, sizeof(uint32_t), st));
     t.stats.bytes_h2d += pf * sizeof(float);
     t.stats.cold_restarts++;
@@ -372,7 +398,7 @@ void Table::issue_early(Prepared& p) {
 // compute that may read those slots), then the loads into their slots.
 void Table::issue_evictions_and_late(Prepared& p) {
   TGS_CUDA(cudaStreamWaitEvent(d2h, ev_comp, 0));
-  const uint64_t pf = (uint64_t)D * B;
+  const uint64_t pf = p_floats;
   bool any_wb = false;
   for (size_t i = 0; i < p.plan.evict_block.size(); ++i)
     if (dirty_host[p.plan.evict_slot[i]]) any_wb = true;
@@ -385,13 +411,17 @@ void Table::issue_evictions_and_late(Prepared& p) {
                                cudaMemcpyDeviceToHost, d2h));
       stats.bytes_d2h += nf * sizeof(float);
       stats.writebacks++;
+      wb_pending[b] = 1;
     }
     dirty_host[s] = 0;
     TGS_CUDA(cudaEventRecord(slot_free_ev[s], d2h));
     slot_has_ev[s] = 1;
     stats.blocks_out++;
   }
-  if (any_wb) copy_timer.end(1, d2h);
+  if (any_wb) {
+    copy_timer.end(1, d2h);
+    TGS_CUDA(cudaEventRecord(ev_wb, d2h));
+  }
   TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
   if (!p.plan.late_block.empty()) {
     copy_timer.begin(0, h2d);
@@ -548,7 +578,7 @@ void Table::flush() {
   TGS_CUDA(cudaStreamSynchronize(comp));
   TGS_CUDA(cudaStreamSynchronize(h2d));
   TGS_CUDA(cudaStreamSynchronize(d2h));
-  const uint64_t pf = (uint64_t)D * B;
+  const uint64_t pf = p_floats;
   for (uint64_t s = 0; s < n_slots; ++s) {
     int64_t b = block_of_slot[s];
     if (b < 0 || !dirty_host[s]) continue;

@@ -30,6 +30,7 @@ struct Table {
   uint32_t B = 0;
   uint64_t C = 0, n_slots = 0;
   uint64_t rec_floats = 0;   // floats per block record (params, m, v)
+  uint64_t p_floats = 0, m_floats = 0;  // params part, one moment part (floats)
   uint64_t V_cap = 0;        // render-list Gaussians capacity
   uint32_t max_items = 0;
 
@@ -69,6 +70,8 @@ struct Table {
   std::vector<cudaEvent_t> slot_free_ev; // n_slots (null = no pending use)
   std::vector<uint8_t> slot_has_ev;
   std::vector<uint8_t> ever_loaded;      // K: for the re-admission counter
+  std::vector<uint8_t> wb_pending;       // K: write-back to the host tier issued, not yet waited on
+  cudaEvent_t ev_wb = nullptr;           // recorded after each write-back batch on d2h
 
   // last computed batch (for the debug getters)
   std::vector<tgs_camera> last_cams;
