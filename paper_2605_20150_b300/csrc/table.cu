@@ -141,6 +141,8 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaMalloc(&rb.scratch, residency_scratch_bytes(K)));
   dalloc(lists_dev, 3 * K + 16);
   TGS_CUDA(cudaMallocHost(&lists_host, (3 * K + 16) * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&kvis_host_pinned, (uint64_t)cfg.max_batch * words * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&r_host_pinned, words * sizeof(uint32_t)));
   dalloc(rl_dev, 3ull * max_items);
   TGS_CUDA(cudaMallocHost(&rl_host, 3ull * max_items * sizeof(uint32_t)));
   const uint64_t pix = (uint64_t)cfg.max_width * cfg.max_height;
@@ -250,7 +252,7 @@ void Table::destroy() {
                  rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, grad_local,
                  loss_dev};
   for (void* p : dev) dfree(p);
-  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host};
+  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned};
   for (void* p : hst)
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
@@ -261,9 +263,10 @@ void Table::destroy() {
     if (s) cudaStreamDestroy(s);
 }
 
-// Stage 1 + Algorithm 1 for a batch: cull, select R_next, derive S+ / S- and
-// the render list, assign slots.  Host waits for the (small) lists.
-void Table::prepare(const tgs_camera* cs, uint32_t J, Prepared& out) {
+// Stage 1 + Algorithm 1 for a batch, enqueued on the control stream: cull,
+// select R_next, derive S+ / S- and the render list; their counts are copied
+// back asynchronously.  prepare_finish() reads the lists and assigns slots.
+void Table::prepare_enqueue(const tgs_camera* cs, uint32_t J, Prepared& out) {
   TGS_CHECK(J >= 1 && J <= cfg.max_batch, TGS_ERR_INVALID, "batch size out of range");
   for (uint32_t j = 0; j < J; ++j) {
     TGS_CHECK(cs[j].width == cs[0].width && cs[j].height == cs[0].height, TGS_ERR_INVALID,
@@ -285,29 +288,35 @@ void Table::prepare(const tgs_camera* cs, uint32_t J, Prepared& out) {
   residency(acc_bits, r_bits, kvis, kvis_union, (int)J, K, ages, C, cfg.lambda, quota, r_next_bits,
             lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl);
   TGS_CUDA(cudaMemcpyAsync(lists_host, rb.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
-  TGS_CUDA(cudaStreamSynchronize(ctl));
-  const uint32_t np = lists_host[0], nm = lists_host[1], nr = lists_host[2];
-  uint32_t cnts[3] = {np, nm, nr};
-  std::vector<uint32_t>* dst[3] = {&out.s_plus, &out.s_minus, &out.render_blocks};
-  for (int q = 0; q < 3; ++q) {
-    if (cnts[q])
-      TGS_CUDA(cudaMemcpyAsync(lists_host, lists_dev + (uint64_t)q * K, cnts[q] * sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, ctl));
-    TGS_CUDA(cudaStreamSynchronize(ctl));
-    dst[q]->assign(lists_host, lists_host + cnts[q]);
-  }
+  TGS_CUDA(cudaMemcpyAsync(kvis_host_pinned, kvis, (uint64_t)J * words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           ctl));
+  TGS_CUDA(cudaEventRecord(ev_ctl, ctl));
   // the selected set becomes the current one for the next selection
   std::swap(r_bits, r_next_bits);
   std::swap(acc_bits, acc_next_bits);
-  // per-camera visible sets of this batch (debug getters)
-  last_kvis_host.resize((uint64_t)J * words);
-  last_r_host.resize(words);
-  TGS_CUDA(cudaMemcpyAsync(last_kvis_host.data(), kvis, (uint64_t)J * words * sizeof(uint32_t),
-                           cudaMemcpyDeviceToHost, ctl));
-  TGS_CUDA(cudaMemcpyAsync(last_r_host.data(), r_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaMemcpyAsync(r_host_pinned, r_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  out.enqueued = true;
+}
+
+void Table::prepare_finish(Prepared& out) {
+  TGS_CHECK(out.enqueued, TGS_ERR_STATE, "prepare_finish without prepare_enqueue");
   TGS_CUDA(cudaStreamSynchronize(ctl));
-  out.kvis_host = last_kvis_host;
-  out.r_host = last_r_host;
+  const uint32_t J = (uint32_t)out.cams.size();
+  const uint32_t np = lists_host[0], nm = lists_host[1], nr = lists_host[2];
+  out.kvis_host.assign(kvis_host_pinned, kvis_host_pinned + (uint64_t)J * words);
+  out.r_host.assign(r_host_pinned, r_host_pinned + words);
+  uint32_t cnts[3] = {np, nm, nr};
+  uint64_t off = 0;
+  for (int q = 0; q < 3; ++q) {
+    if (cnts[q])
+      TGS_CUDA(cudaMemcpyAsync(lists_host + off, lists_dev + (uint64_t)q * K, cnts[q] * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, ctl));
+    off += cnts[q];
+  }
+  TGS_CUDA(cudaStreamSynchronize(ctl));
+  out.s_plus.assign(lists_host, lists_host + np);
+  out.s_minus.assign(lists_host + np, lists_host + np + nm);
+  out.render_blocks.assign(lists_host + np + nm, lists_host + np + nm + nr);
 
   // ---- slot assignment: free slots (ascending) for S+ in ascending id order,
   // the rest into the slots that S- frees (ascending)
@@ -507,6 +516,8 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp);
     adam_render_list(rl, grad_local, touched, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp);
     timer.end(StageTimer::ADAM, comp);
+    // the next batch's cull (control stream) reads the bounds first
+    TGS_CUDA(cudaStreamWaitEvent(comp, ev_ctl, 0));
     timer.begin(StageTimer::BOUNDS, comp);
     block_bounds(rl, item_touched, spheres, comp);
     timer.end(StageTimer::BOUNDS, comp);
@@ -534,7 +545,8 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   if (!(prep.valid && same_cams(prep.cams, cs, J))) {
     // reactive path: select and stream this batch's working set now
     Prepared p;
-    prepare(cs, J, p);
+    prepare_enqueue(cs, J, p);
+    prepare_finish(p);
     issue_early(p);
     issue_evictions_and_late(p);
     prep = std::move(p);
@@ -543,15 +555,13 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   prep = Prepared();
   Prepared nxt;
   const bool prefetch = cfg.prefetch_mode == 1 && next && nJ >= 1;
-  if (prefetch) {
-    // Algorithm 1 for batch t+1 while batch t computes: selection uses the
-    // bounds as of the start of step t; incoming blocks go to spare slots now
-    prepare(next, nJ, nxt);
-    if (cfg.overlap) issue_early(nxt);
-  }
+  // Algorithm 1 for batch t+1 runs on the control stream while batch t is
+  // enqueued; it sees the bounds as of the start of step t
+  if (prefetch) prepare_enqueue(next, nJ, nxt);
   compute(cur, targets_dev, targets_host, user, true, nullptr);
   if (prefetch) {
-    if (!cfg.overlap) issue_early(nxt);
+    prepare_finish(nxt);
+    issue_early(nxt);
     issue_evictions_and_late(nxt);
     prep = std::move(nxt);
   }
@@ -566,7 +576,8 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
 
 void Table::render(const tgs_camera& cam, float* image_dev, cudaStream_t user) {
   Prepared p;
-  prepare(&cam, 1, p);
+  prepare_enqueue(&cam, 1, p);
+  prepare_finish(p);
   issue_early(p);
   issue_evictions_and_late(p);
   compute(p, nullptr, nullptr, user, false, image_dev);

@@ -16,6 +16,7 @@ struct CopyPlan {
 
 struct Prepared {
   bool valid = false;
+  bool enqueued = false;
   std::vector<tgs_camera> cams;
   std::vector<uint32_t> render_blocks;  // R & K of the batch, ascending
   std::vector<uint32_t> render_slots;   // their slots, fixed when the batch is selected
@@ -51,6 +52,8 @@ struct Table {
   ResidencyBuffers rb{};
   uint32_t* lists_dev = nullptr;   // s_plus | s_minus | render (K each)
   uint32_t* lists_host = nullptr;  // pinned
+  uint32_t* kvis_host_pinned = nullptr;  // pinned, max_batch x words
+  uint32_t* r_host_pinned = nullptr;     // pinned, words
   uint32_t* rl_dev = nullptr;      // item_slot | item_count | item_block
   uint32_t* rl_host = nullptr;     // pinned
   std::vector<CamState> cams;
@@ -94,7 +97,8 @@ struct Table {
   void fill_host(const float* params);
   void init_spheres();
   void set_params(const float* params);
-  void prepare(const tgs_camera* cams, uint32_t J, Prepared& out);
+  void prepare_enqueue(const tgs_camera* cams, uint32_t J, Prepared& out);
+  void prepare_finish(Prepared& out);
   void issue_early(Prepared& p);
   void issue_evictions_and_late(Prepared& p);
   void compute(const Prepared& p, const float* targets_dev, const float* targets_host, cudaStream_t user,
