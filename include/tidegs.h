@@ -192,6 +192,9 @@ typedef struct tgs_stats {
   uint64_t kernel_launches;
   double stall_ms;          /* compute stream waiting for incoming blocks */
   double h2d_ms, d2h_ms;    /* CUDA-event time of the copy batches on the copy streams */
+  uint64_t demand_blocks;   /* sum over computed batches of their visible blocks */
+  uint64_t demand_hits;     /* ... of those already resident before the batch's own selection */
+  uint64_t predicted_blocks; /* blocks streamed in on a prediction (learned prefetch) */
   uint64_t last_pairs, last_visible, last_render_blocks;
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
@@ -205,6 +208,50 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
  * the accumulators after reading. */
 tgs_status tgs_set_stage_timing(tgs_table* t, int enable);
 tgs_status tgs_get_stage_ms(tgs_table* t, double* ms8, uint64_t* counts8, int reset);
+
+/* Level-1 visibility only (Sec. 3.3, Eq. Kt_def) of J cameras against the
+ * current block bounds: vis_host (host, J x K bytes) gets 1 for visible
+ * blocks.  Used to log visibility for the learned predictor. */
+tgs_status tgs_visible_blocks(tgs_table* t, const tgs_camera* cams, uint32_t J, uint8_t* vis_host);
+
+/* ---------------------------------------------------------------------------
+ * Learned block-prefetch predictor (the paper has none; it is the learned
+ * prefetch form of this implementation).  A 3-layer MLP, 102 -> 256 -> 256
+ * -> 4 (ReLU, sigmoid outputs), predicts for each block whether it will be
+ * visible 1..4 iterations ahead from the last 8 camera poses (each as the
+ * rotation and translation / zfar of that camera in the current camera's
+ * frame) and 6 block features (centroid in the current camera frame / zfar,
+ * radius / zfar, distance / zfar, radius / max(distance, radius)).  Layer 2
+ * runs on the tensor cores (BF16 weights and activations, FP32 accumulation).
+ * Parameters: flat FP32 [W1 (102 x 256), b1 (256), W2 (256 x 256), b2 (256),
+ * W3 (256 x 4), b3 (4)], row-major, input index first.
+ * ------------------------------------------------------------------------- */
+typedef struct tgs_mlp tgs_mlp;
+/* max_blocks: largest K; seed: initial weights N(0, 1/sqrt(fan_in)), zero biases. */
+tgs_status tgs_mlp_create(uint64_t max_blocks, uint32_t seed, tgs_mlp** out);
+void tgs_mlp_destroy(tgs_mlp* m);
+uint64_t tgs_mlp_num_params(void);
+tgs_status tgs_mlp_get_params(tgs_mlp* m, float* params_host);
+tgs_status tgs_mlp_set_params(tgs_mlp* m, const float* params_host);
+/* Logits (device, K x 4) of K blocks with spheres (device, K x 4: cx, cy, cz,
+ * r) for the camera history hist (host, 8 cameras, oldest first, the last the
+ * current one). */
+tgs_status tgs_mlp_forward(tgs_mlp* m, const float* spheres_dev, uint64_t K, const tgs_camera* hist,
+                           float* logits_dev, void* stream);
+/* One training step on K labelled blocks (labels_dev: device, K x 4, 1 = visible
+ * at t+h): forward, BCE with pos_weight (mean over K x 4), backward, and, if
+ * apply != 0, AdamW (lr, weight_decay, betas 0.9 / 0.999, eps 1e-8).
+ * loss_out (host) gets the loss before the update; grads_host (host, flat, may
+ * be NULL) the gradient. */
+tgs_status tgs_mlp_train_step(tgs_mlp* m, const float* spheres_dev, uint64_t K, const tgs_camera* hist,
+                              const float* labels_dev, float pos_weight, float lr, float weight_decay, int apply,
+                              float* loss_out, float* grads_host, void* stream);
+/* Attaches a predictor to a table for prefetch_mode 2: after each step's
+ * culling, blocks whose predicted probability exceeds `threshold` for a
+ * horizon in horizon_mask (bit h-1 = t+h) are selected by Algorithm 1 and
+ * streamed while the step computes; the next step culls its actual batch
+ * and fetches what was missed.  The predictor must outlive its use. */
+tgs_status tgs_set_predictor(tgs_table* t, tgs_mlp* m, float threshold, uint32_t horizon_mask);
 
 /* ---------------------------------------------------------------------------
  * Resident (fully in-HBM) rasteriser for autograd frameworks: the standard

@@ -48,7 +48,8 @@ class tgs_stats(ctypes.Structure):
                 ("blocks_in", ctypes.c_uint64), ("blocks_out", ctypes.c_uint64), ("writebacks", ctypes.c_uint64),
                 ("readmissions", ctypes.c_uint64), ("cold_restarts", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("stall_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
-                ("d2h_ms", ctypes.c_double), ("last_pairs", ctypes.c_uint64),
+                ("d2h_ms", ctypes.c_double), ("demand_blocks", ctypes.c_uint64), ("demand_hits", ctypes.c_uint64),
+                ("predicted_blocks", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64)]
 
 
@@ -75,6 +76,16 @@ _SIGS = {
     "tgs_get_stats": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_stats)]),
     "tgs_set_stage_timing": (ctypes.c_int32, [_VP, ctypes.c_int]),
     "tgs_get_stage_ms": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int]),
+    "tgs_visible_blocks": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_camera), _U32, _VP]),
+    "tgs_mlp_create": (ctypes.c_int32, [_U64, _U32, ctypes.POINTER(_VP)]),
+    "tgs_mlp_destroy": (None, [_VP]),
+    "tgs_mlp_num_params": (_U64, []),
+    "tgs_mlp_get_params": (ctypes.c_int32, [_VP, _VP]),
+    "tgs_mlp_set_params": (ctypes.c_int32, [_VP, _VP]),
+    "tgs_mlp_forward": (ctypes.c_int32, [_VP, _VP, _U64, ctypes.POINTER(tgs_camera), _VP, _VP]),
+    "tgs_mlp_train_step": (ctypes.c_int32, [_VP, _VP, _U64, ctypes.POINTER(tgs_camera), _VP, _F, _F, _F, ctypes.c_int,
+                                            ctypes.POINTER(_F), _VP, _VP]),
+    "tgs_set_predictor": (ctypes.c_int32, [_VP, _VP, _F, _U32]),
     "tgs_raster_create": (ctypes.c_int32, [_U64, _U32, _U32, ctypes.POINTER(_VP)]),
     "tgs_raster_destroy": (None, [_VP]),
     "tgs_raster_forward": (ctypes.c_int32, [_VP, _VP, _U64, _U32, ctypes.POINTER(tgs_camera), _VP, _VP, _VP]),
@@ -274,10 +285,60 @@ class TideTable:
         _check(load().tgs_get_stage_ms(self.h, _ptr(ms), _ptr(cnt), int(reset)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.STAGES)}
 
+    def visible_blocks(self, cams):
+        out = np.zeros((len(cams), self.K), np.uint8)
+        _check(load().tgs_visible_blocks(self.h, camera_array(cams), len(cams), _ptr(out)))
+        return out
+
+    def set_predictor(self, mlp, threshold=0.5, horizon_mask=1):
+        _check(load().tgs_set_predictor(self.h, mlp.h if mlp is not None else None, threshold, horizon_mask))
+        self._predictor = mlp  # keep alive
+
     def stats(self):
         s = tgs_stats()
         _check(load().tgs_get_stats(self.h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+class Predictor:
+    """Learned block-prefetch MLP (tgs_mlp_*)."""
+
+    def __init__(self, max_blocks, seed=0):
+        h = ctypes.c_void_p()
+        _check(load().tgs_mlp_create(max_blocks, seed, ctypes.byref(h)))
+        self.h = h
+        self.n_params = load().tgs_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tgs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(load().tgs_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, flat):
+        _check(load().tgs_mlp_set_params(self.h, _ptr(np.ascontiguousarray(flat, np.float32))))
+
+    def forward(self, spheres_dev, hist, logits_dev):
+        _check(load().tgs_mlp_forward(self.h, _ptr(spheres_dev), spheres_dev.shape[0], camera_array(hist),
+                                      _ptr(logits_dev), _stream()))
+
+    def train_step(self, spheres_dev, hist, labels_dev, pos_weight, lr=1e-3, wd=1e-4, apply=True, want_grads=False):
+        loss = _F()
+        g = np.zeros(self.n_params, np.float32) if want_grads else None
+        _check(load().tgs_mlp_train_step(self.h, _ptr(spheres_dev), spheres_dev.shape[0], camera_array(hist),
+                                         _ptr(labels_dev), pos_weight, lr, wd, int(apply), ctypes.byref(loss),
+                                         _ptr(g), _stream()))
+        return (loss.value, g) if want_grads else loss.value
 
 
 # ---------------------------------------------------------------------------

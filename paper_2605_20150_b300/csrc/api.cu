@@ -87,6 +87,9 @@ struct tgs_table {
 struct tgs_raster {
   Raster r;
 };
+struct tgs_mlp {
+  Mlp m;
+};
 
 extern "C" {
 
@@ -376,6 +379,90 @@ tgs_status tgs_get_stage_ms(tgs_table* t, double* ms8, uint64_t* counts8, int re
       if (counts8) counts8[i] = t->t.timer.count[i];
     }
     if (reset) t->t.timer.reset();
+  });
+}
+
+tgs_status tgs_visible_blocks(tgs_table* t, const tgs_camera* cams, uint32_t J, uint8_t* vis_host) {
+  return guard([&] {
+    TGS_CHECK(t && cams && vis_host, TGS_ERR_INVALID, "tgs_visible_blocks: null argument");
+    t->t.cull_only(cams, J, vis_host);
+  });
+}
+
+tgs_status tgs_mlp_create(uint64_t max_blocks, uint32_t seed, tgs_mlp** out) {
+  return guard([&] {
+    TGS_CHECK(out && max_blocks > 0, TGS_ERR_INVALID, "tgs_mlp_create: bad arguments");
+    *out = nullptr;
+    tgs_mlp* m = new tgs_mlp();
+    try {
+      mlp_alloc(m->m, max_blocks, seed);
+    } catch (...) {
+      mlp_free(m->m);
+      delete m;
+      throw;
+    }
+    *out = m;
+  });
+}
+
+void tgs_mlp_destroy(tgs_mlp* m) {
+  if (!m) return;
+  mlp_free(m->m);
+  delete m;
+}
+
+uint64_t tgs_mlp_num_params(void) { return MLP_NPARAM; }
+
+tgs_status tgs_mlp_get_params(tgs_mlp* m, float* host) {
+  return guard([&] {
+    TGS_CHECK(m && host, TGS_ERR_INVALID, "tgs_mlp_get_params: null argument");
+    TGS_CUDA(cudaMemcpy(host, m->m.params, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+tgs_status tgs_mlp_set_params(tgs_mlp* m, const float* host) {
+  return guard([&] {
+    TGS_CHECK(m && host, TGS_ERR_INVALID, "tgs_mlp_set_params: null argument");
+    TGS_CUDA(cudaMemcpy(m->m.params, host, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    TGS_CUDA(cudaMemset(m->m.m, 0, MLP_NPARAM * sizeof(float)));
+    TGS_CUDA(cudaMemset(m->m.v, 0, MLP_NPARAM * sizeof(float)));
+    m->m.step = 0;
+    mlp_refresh_bf16(m->m, 0);
+    TGS_CUDA(cudaDeviceSynchronize());
+  });
+}
+
+tgs_status tgs_mlp_forward(tgs_mlp* m, const float* spheres_dev, uint64_t K, const tgs_camera* hist,
+                           float* logits_dev, void* stream) {
+  return guard([&] {
+    TGS_CHECK(m && spheres_dev && hist && logits_dev, TGS_ERR_INVALID, "tgs_mlp_forward: null argument");
+    mlp_forward(m->m, reinterpret_cast<const float4*>(spheres_dev), K, hist, logits_dev, false,
+                (cudaStream_t)stream);
+  });
+}
+
+tgs_status tgs_mlp_train_step(tgs_mlp* m, const float* spheres_dev, uint64_t K, const tgs_camera* hist,
+                              const float* labels_dev, float pos_weight, float lr, float weight_decay, int apply,
+                              float* loss_out, float* grads_host, void* stream) {
+  return guard([&] {
+    TGS_CHECK(m && spheres_dev && hist && labels_dev, TGS_ERR_INVALID, "tgs_mlp_train_step: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    mlp_forward(m->m, reinterpret_cast<const float4*>(spheres_dev), K, hist, nullptr, true, s);
+    float l = mlp_train_step(m->m, K, labels_dev, pos_weight, lr, weight_decay, apply != 0, s);
+    if (loss_out) *loss_out = l;
+    if (grads_host) TGS_CUDA(cudaMemcpy(grads_host, m->m.grads, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+tgs_status tgs_set_predictor(tgs_table* t, tgs_mlp* m, float threshold, uint32_t horizon_mask) {
+  return guard([&] {
+    TGS_CHECK(t, TGS_ERR_INVALID, "tgs_set_predictor: null table");
+    TGS_CHECK(!m || m->m.max_rows >= t->t.K, TGS_ERR_CAPACITY, "predictor smaller than the table's block count");
+    TGS_CHECK(threshold > 0.f && threshold < 1.f && (horizon_mask & 15u), TGS_ERR_INVALID,
+              "threshold must be in (0, 1) and horizon_mask non-empty");
+    t->t.predictor = m ? &m->m : nullptr;
+    t->t.pred_threshold = threshold;
+    t->t.pred_mask = horizon_mask & 15u;
   });
 }
 

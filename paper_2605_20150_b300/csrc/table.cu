@@ -283,19 +283,60 @@ void Table::prepare_enqueue(const tgs_camera* cs, uint32_t J, Prepared& out) {
   TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
   TGS_CUDA(cudaMemcpyAsync(planes_dev, planes_host, J * sizeof(Planes), cudaMemcpyHostToDevice, ctl));
   cull_blocks(spheres, K, planes_dev, (int)J, kvis, kvis_union, ctl);
+  select_enqueue(J, out, true);
+}
+
+// Learned prefetch: the predictor's visible set for the coming iterations
+// (probability above the threshold for a horizon in pred_mask) replaces the
+// culled set of a known next batch.  Ages and the accessed set are left alone:
+// nothing has been rendered from the prediction yet.
+void Table::prepare_enqueue_predicted(Prepared& out) {
+  TGS_CHECK(predictor && !hist.empty(), TGS_ERR_STATE, "no predictor or camera history");
+  out = Prepared();
+  out.predicted = true;
+  tgs_camera h[MLP_HIST];
+  for (int s = 0; s < MLP_HIST; ++s) {
+    int idx = (int)hist.size() - MLP_HIST + s;
+    h[s] = hist[idx < 0 ? 0 : idx];
+  }
+  TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+  mlp_forward(*predictor, spheres, K, h, nullptr, false, ctl);
+  mlp_threshold(predictor->z3, K, pred_mask, pred_threshold, kvis, ctl);
+  TGS_CUDA(cudaMemcpyAsync(kvis_union, kvis, words * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctl));
+  select_enqueue(1, out, false);
+}
+
+// Algorithm 1 on the visible sets in kvis (J rows); counts and sets are copied
+// back asynchronously.  accessed = false: a prediction (no ages, no access).
+void Table::select_enqueue(uint32_t J, Prepared& out, bool accessed) {
   uint64_t quota = cfg.quota == 0xFFFFFFFFu ? C / (2 * J) : cfg.quota;
   if (quota * J > C) quota = C / J;
   residency(acc_bits, r_bits, kvis, kvis_union, (int)J, K, ages, C, cfg.lambda, quota, r_next_bits,
-            lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl);
+            lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl, accessed);
   TGS_CUDA(cudaMemcpyAsync(lists_host, rb.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
   TGS_CUDA(cudaMemcpyAsync(kvis_host_pinned, kvis, (uint64_t)J * words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                            ctl));
   TGS_CUDA(cudaEventRecord(ev_ctl, ctl));
   // the selected set becomes the current one for the next selection
   std::swap(r_bits, r_next_bits);
-  std::swap(acc_bits, acc_next_bits);
+  if (accessed) std::swap(acc_bits, acc_next_bits);
   TGS_CUDA(cudaMemcpyAsync(r_host_pinned, r_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
   out.enqueued = true;
+}
+
+void Table::cull_only(const tgs_camera* cs, uint32_t J, uint8_t* vis_host) {
+  TGS_CHECK(J >= 1 && J <= cfg.max_batch, TGS_ERR_INVALID, "batch size out of range");
+  for (uint32_t j = 0; j < J; ++j) planes_host[j] = frustum_planes(cs[j], cfg.cull_margin_px);
+  TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+  TGS_CUDA(cudaMemcpyAsync(planes_dev, planes_host, J * sizeof(Planes), cudaMemcpyHostToDevice, ctl));
+  // the union buffer of the selection is not touched: use the residency
+  // scratch for the per-camera words
+  cull_blocks(spheres, K, planes_dev, (int)J, rb.tmp, rb.tmp2, ctl);
+  std::vector<uint32_t> w((uint64_t)J * words);
+  TGS_CUDA(cudaMemcpyAsync(w.data(), rb.tmp, w.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaStreamSynchronize(ctl));
+  for (uint32_t j = 0; j < J; ++j)
+    for (uint64_t k = 0; k < K; ++k) vis_host[(uint64_t)j * K + k] = (w[(uint64_t)j * words + (k >> 5)] >> (k & 31)) & 1u;
 }
 
 void Table::prepare_finish(Prepared& out) {
@@ -317,6 +358,20 @@ void Table::prepare_finish(Prepared& out) {
   out.s_plus.assign(lists_host, lists_host + np);
   out.s_minus.assign(lists_host + np, lists_host + np + nm);
   out.render_blocks.assign(lists_host + np + nm, lists_host + np + nm + nr);
+  // demand hit counters: blocks of an actual batch already resident before
+  // its selection (for the learned mode: after the prediction's copies)
+  if (!out.predicted) {
+    if (r_host_prev.size() != words) r_host_prev.assign(words, 0u);
+    for (uint64_t w = 0; w < words; ++w) {
+      uint32_t u = 0;
+      for (uint32_t j = 0; j < J; ++j) u |= out.kvis_host[(uint64_t)j * words + w];
+      stats.demand_blocks += __builtin_popcount(u);
+      stats.demand_hits += __builtin_popcount(u & r_host_prev[w]);
+    }
+  } else {
+    stats.predicted_blocks += np;
+  }
+  r_host_prev = out.r_host;
 
   // ---- slot assignment: free slots (ascending) for S+ in ascending id order,
   // the rest into the slots that S- frees (ascending)
@@ -554,12 +609,18 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   Prepared cur = std::move(prep);
   prep = Prepared();
   Prepared nxt;
+  for (uint32_t j = 0; j < J; ++j) {
+    hist.push_back(cs[j]);
+    if (hist.size() > MLP_HIST) hist.pop_front();
+  }
   const bool prefetch = cfg.prefetch_mode == 1 && next && nJ >= 1;
+  const bool learned = cfg.prefetch_mode == 2 && predictor != nullptr;
   // Algorithm 1 for batch t+1 runs on the control stream while batch t is
   // enqueued; it sees the bounds as of the start of step t
   if (prefetch) prepare_enqueue(next, nJ, nxt);
+  if (learned) prepare_enqueue_predicted(nxt);
   compute(cur, targets_dev, targets_host, user, true, nullptr);
-  if (prefetch) {
+  if (prefetch || learned) {
     prepare_finish(nxt);
     issue_early(nxt);
     issue_evictions_and_late(nxt);

@@ -3,6 +3,9 @@
 #pragma once
 #include <vector>
 
+#include <deque>
+
+#include "predictor.cuh"
 #include "raster.cuh"
 #include "visibility.cuh"
 
@@ -17,6 +20,7 @@ struct CopyPlan {
 struct Prepared {
   bool valid = false;
   bool enqueued = false;
+  bool predicted = false;  // selection for a predicted (learned) visible set
   std::vector<tgs_camera> cams;
   std::vector<uint32_t> render_blocks;  // R & K of the batch, ascending
   std::vector<uint32_t> render_slots;   // their slots, fixed when the batch is selected
@@ -89,6 +93,12 @@ struct Table {
   bool stall_pending = false;
 
   tgs_stats stats{};
+  // learned prefetch
+  Mlp* predictor = nullptr;
+  float pred_threshold = 0.5f;
+  uint32_t pred_mask = 1u;
+  std::deque<tgs_camera> hist;
+  std::vector<uint32_t> r_host_prev;  // resident set before the latest selection
   StageTimer timer;
   StageTimer copy_timer;  // stage 0: H2D batches, stage 1: D2H batches (always on)
 
@@ -98,6 +108,9 @@ struct Table {
   void init_spheres();
   void set_params(const float* params);
   void prepare_enqueue(const tgs_camera* cams, uint32_t J, Prepared& out);
+  void prepare_enqueue_predicted(Prepared& out);
+  void select_enqueue(uint32_t J, Prepared& out, bool accessed);
+  void cull_only(const tgs_camera* cams, uint32_t J, uint8_t* vis_host);
   void prepare_finish(Prepared& out);
   void issue_early(Prepared& p);
   void issue_evictions_and_late(Prepared& p);

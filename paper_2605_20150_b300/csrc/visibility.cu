@@ -104,14 +104,16 @@ __device__ __forceinline__ bool bit(const uint32_t* w, uint64_t k) { return (w[k
 // ages, candidate flags and inverted score keys
 __global__ void k_res_score(const uint32_t* __restrict__ k_acc, const uint32_t* __restrict__ r_cur,
                             const uint32_t* __restrict__ k_next_union, uint64_t K, uint32_t* __restrict__ ages,
-                            float lambda, uint32_t* __restrict__ flag, uint32_t* __restrict__ key) {
+                            float lambda, int age_update, uint32_t* __restrict__ flag, uint32_t* __restrict__ key) {
   uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   uint32_t a = ages[k];
   bool r = bit(r_cur, k), kn = bit(k_next_union, k);
-  if (r && bit(k_acc, k)) a = 0;
-  else if (a < 126) a += 1;
-  ages[k] = a;
+  if (age_update) {
+    if (r && bit(k_acc, k)) a = 0;
+    else if (a < 126) a += 1;
+    ages[k] = a;
+  }
   float lam = lambda;
   float oml = __fsub_rn(1.f, lam);
   float t = __fmul_rn(oml, ldexpf(1.f, -(int)a));
@@ -279,11 +281,11 @@ size_t residency_scratch_bytes(uint64_t K) {
 void residency(const uint32_t* k_acc, const uint32_t* r_cur, const uint32_t* k_next, const uint32_t* k_next_union,
                int J, uint64_t K, uint32_t* ages, uint64_t capacity, float lambda, uint64_t quota, uint32_t* r_next,
                uint32_t* s_plus, uint32_t* s_minus, uint32_t* render, uint32_t* acc_out, ResidencyBuffers& rb,
-               cudaStream_t s) {
+               cudaStream_t s, bool age_update) {
   const uint64_t words = (K + 31) / 32;
   const unsigned gk = div_up(K, 256);
   uint32_t* cnt = rb.counters;
-  k_res_score<<<gk, 256, 0, s>>>(k_acc, r_cur, k_next_union, K, ages, lambda, rb.flag, rb.tmp);
+  k_res_score<<<gk, 256, 0, s>>>(k_acc, r_cur, k_next_union, K, ages, lambda, age_update ? 1 : 0, rb.flag, rb.tmp);
   TGS_LAUNCHED();
   exclusive_scan_u32(rb.flag, rb.pos, cnt + 3, K, rb.scratch, s);
   // non-candidates keep the largest key and sort after every candidate (the

@@ -49,11 +49,12 @@ struct ResidencyBuffers {
 // asc) order, fills to capacity by the same order, and writes r_next.
 // Outputs (device): lists s_plus, s_minus, render (r_next & union k_next),
 // ascending, with counts in counters[0..2]; acc_out = render as a bitmap
-// (the blocks this batch will access).
+// (the blocks this batch will access).  age_update = false leaves the ages
+// unchanged (a selection for predicted, not accessed, blocks).
 void residency(const uint32_t* k_acc, const uint32_t* r_cur, const uint32_t* k_next, const uint32_t* k_next_union,
                int J, uint64_t K, uint32_t* ages, uint64_t capacity, float lambda, uint64_t quota,
                uint32_t* r_next, uint32_t* s_plus, uint32_t* s_minus, uint32_t* render, uint32_t* acc_out,
-               ResidencyBuffers& rb, cudaStream_t s);
+               ResidencyBuffers& rb, cudaStream_t s, bool age_update = true);
 
 size_t residency_scratch_bytes(uint64_t K);
 
