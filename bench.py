@@ -235,12 +235,26 @@ def link_peak(torch, mb=256, reps=10):
     return out
 
 
+def psnr(img, ref):
+    mse = float(((img - ref) ** 2).mean())
+    return 10.0 * np.log10(1.0 / max(mse, 1e-12))
+
+
 def run_street(args, rank, world, local):
     """Out-of-core street workload: 100M Gaussians in 4,096-Gaussian Morton
-    blocks over a 4 km street grid, full FP32 state (params + 2 Adam moments,
-    708 B per Gaussian) in pinned host memory, HBM cache capped at 24 GB,
-    1600x900 cameras along a street-level drive at 1.5 m, batch 1, exact
-    next-batch prefetch.  Targets are renders of the unperturbed scene."""
+    blocks over a 4 km street grid, HBM cache capped at 24 GB, 500 cameras at
+    1600x900 along a street-level drive at 1.5 m, batch 1.  Three forms run on
+    the same scene, cameras and targets (renders of the unperturbed scene),
+    each from the same perturbed start:
+      fp32_reactive  FP32 params + moments in pinned host memory (708 B per
+                     Gaussian), each batch's delta selected and streamed at its
+                     own step (copies exposed);
+      bf16_learned   SH-rest and moments BF16 (382 B), a predictor trained on
+                     the visibility logged along this drive streams the blocks
+                     of the coming iterations while the current one computes;
+      bf16_exact     BF16, the paper's exact next-batch prefetch.
+    Every 10th camera is held out; PSNR of the held-out renders after each
+    form's timed steps gives the quality gap."""
     import torch
     import paper_2605_20150_b300 as tgs
     torch.cuda.set_device(local)
@@ -259,75 +273,127 @@ def run_street(args, rank, world, local):
     torch.cuda.empty_cache()
     W, H = cams[0]["width"], cams[0]["height"]
     cache = int(24e9 // (4096 * 708))
-    tcfg = dict(block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache, spare_slots=512,
-                prefetch_mode=1, moments_policy=0, loss=0)
-    table = tgs.TideTable(host, **tcfg)
-    t_create = time.perf_counter() - t0
+    base = dict(block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache, spare_slots=512,
+                moments_policy=0, loss=0)
+    table = tgs.TideTable(host, prefetch_mode=0, **base)
     targets = torch.empty(nc, H, W, 3, device=dev, dtype=torch.float32)
     for i, c in enumerate(cams):
         table.render(c, targets[i])
+    vis = np.concatenate([table.visible_blocks([c]) for c in cams])
+    spheres = torch.tensor(table.spheres(), device=dev)
     torch.cuda.synchronize()
     chunk = 1 << 24
     for a in range(0, n, chunk):
         rows = torch.from_numpy(host[a:a + chunk]).to(dev)
         scenes.t_perturb_(rows, 2003, a, mean_std=0.02 * spacing)
         host[a:a + chunk] = rows.cpu().numpy()
-    table.set_params(host)
+    train_ids = [i for i in range(nc) if i % 10 != 0]
+    held = [i for i in range(0, nc, 10)][:10]
     t_setup = time.perf_counter() - t0
-
-    def one(t):
-        table.step([cams[t % nc]], targets[t % nc:t % nc + 1], next_cams=[cams[(t + 1) % nc]], want_loss=False)
-
-    for t in range(args.warmup):
-        one(t)
-    table.sync()
-    st0 = table.stats()
-    table.stage_timing(True)
-    table.stage_ms(reset=True)
-    clk = ClockSampler(local)
-    clk.start()
     s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(s)
-    for t in range(args.warmup, args.warmup + args.steps):
-        one(t)
-    e1.record(s)
-    table.sync()
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    stages = table.stage_ms(reset=True)
-    table.stage_timing(False)
-    st = table.stats()
-    delta = {k: st[k] - st0[k] for k in ("bytes_h2d", "bytes_d2h", "blocks_in", "blocks_out", "writebacks",
-                                         "readmissions", "stall_ms", "h2d_ms", "d2h_ms", "kernel_launches")}
-    rec = table.camera_record(0, W, H)
+
+    def timed(tab, label):
+        tab.set_params(host)
+        seq = train_ids
+
+        def one(k):
+            i = seq[k % len(seq)]
+            j = seq[(k + 1) % len(seq)]
+            tab.step([cams[i]], targets[i:i + 1], next_cams=[cams[j]], want_loss=False)
+
+        for k in range(args.warmup):
+            one(k)
+        tab.sync()
+        st0 = tab.stats()
+        tab.stage_timing(True)
+        tab.stage_ms(reset=True)
+        clk = ClockSampler(local)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for k in range(args.warmup, args.warmup + args.steps):
+            one(k)
+        e1.record(s)
+        tab.sync()
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        stages = tab.stage_ms(reset=True)
+        tab.stage_timing(False)
+        st = tab.stats()
+        d = {k: st[k] - st0[k] for k in ("bytes_h2d", "bytes_d2h", "blocks_in", "blocks_out", "writebacks",
+                                         "readmissions", "stall_ms", "h2d_ms", "d2h_ms", "kernel_launches",
+                                         "demand_blocks", "demand_hits", "predicted_blocks")}
+        img = torch.empty(H, W, 3, device=dev)
+        ps = []
+        for i in held:
+            tab.render(cams[i], img)
+            ps.append(psnr(img.cpu().numpy(), targets[i].cpu().numpy()))
+        rec = tab.camera_record(0, W, H) if label == "bf16_learned" else None
+        return dict(ms=ms, stages=stages, stats=st, delta=d, clocks=clocks, psnr=float(np.mean(ps)), rec=rec,
+                    iters=1e3 * args.steps / ms)
+
+    forms = {}
+    forms["fp32_reactive"] = timed(table, "fp32_reactive")
+    table.close()
+    del table
+    tb = tgs.TideTable(host, prefetch_mode=2, host_bf16=1, stochastic_round=1, **base)
+    # predictor trained on the visibility logged along the drive (training cameras)
+    K = vis.shape[1]
+    pred = tgs.Predictor(K, seed=11)
+    pos = max(vis.mean(), 1e-6)
+    t_train = time.perf_counter()
+    for epoch in range(3):
+        for t in np.random.default_rng(epoch).permutation(nc):
+            hist = [cams[max(t - 7 + q, 0)] for q in range(8)]
+            lab = np.stack([vis[min(t + h, nc - 1)] for h in range(1, 5)], 1).astype(np.float32)
+            pred.train_step(spheres, hist, torch.tensor(lab, device=dev), pos_weight=float((1 - pos) / pos), lr=2e-3)
+    t_train = time.perf_counter() - t_train
+    tb.set_predictor(pred, threshold=0.3, horizon_mask=0b11)
+    forms["bf16_learned"] = timed(tb, "bf16_learned")
+    tb.set_prefetch_mode(1)
+    forms["bf16_exact"] = timed(tb, "bf16_exact")
+    tb.set_prefetch_mode(2)
+    head = forms["bf16_learned"]
     peak = link_peak(torch)
-    # end to end with host targets and the loss read back each step
+    # end to end (headline form) with host targets and the loss read back each step
     host_t = torch.empty(min(nc, 64), H, W, 3, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets[:host_t.shape[0]].cpu())
     host_np = host_t.numpy()
     n_e2e = max(5, args.steps // 2)
-    base = args.warmup + args.steps
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for t in range(n_e2e):
-        k = (base + t) % host_np.shape[0]
-        table.step([cams[(base + t) % nc]], host_np[k:k + 1], next_cams=[cams[(base + t + 1) % nc]], want_loss=True)
+    for k in range(n_e2e):
+        i = k % host_np.shape[0]
+        tb.step([cams[i]], host_np[i:i + 1], next_cams=[cams[i + 1]], want_loss=True)
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
-    link = {"peak_gbs": peak, "bytes_h2d_per_step": delta["bytes_h2d"] / args.steps,
-            "bytes_d2h_per_step": delta["bytes_d2h"] / args.steps,
-            "h2d_gbs_while_copying": round(delta["bytes_h2d"] / max(delta["h2d_ms"], 1e-9) / 1e6, 2),
-            "d2h_gbs_while_copying": round(delta["bytes_d2h"] / max(delta["d2h_ms"], 1e-9) / 1e6, 2),
-            "h2d_frac_of_peak": round(delta["bytes_h2d"] / max(delta["h2d_ms"], 1e-9) / 1e6 / peak["h2d"], 4),
-            "stall_ms_per_step": round(delta["stall_ms"] / args.steps, 4),
-            "blocks_in_per_step": delta["blocks_in"] / args.steps, "blocks_out_per_step": delta["blocks_out"] / args.steps,
-            "writebacks": delta["writebacks"], "readmissions": delta["readmissions"]}
-    return dict(ms=ms, stages=stages, stats=st, launches=delta["kernel_launches"], clocks=clocks, rec=rec,
-                table=table, cams=cams, W=W, H=H, e2e_ms=e2e_ms, bytes_in=H * W * 3 * 4, link=link, n=n, nc=nc,
-                cache_blocks=cache, setup_s=round(t_setup, 1), create_s=round(t_create, 1), host=host)
+    d = head["delta"]
+    link = {"peak_gbs": peak, "bytes_h2d_per_step": d["bytes_h2d"] / args.steps,
+            "bytes_d2h_per_step": d["bytes_d2h"] / args.steps,
+            "h2d_gbs_while_copying": round(d["bytes_h2d"] / max(d["h2d_ms"], 1e-9) / 1e6, 2),
+            "d2h_gbs_while_copying": round(d["bytes_d2h"] / max(d["d2h_ms"], 1e-9) / 1e6, 2),
+            "h2d_frac_of_peak": round(d["bytes_h2d"] / max(d["h2d_ms"], 1e-9) / 1e6 / peak["h2d"], 4),
+            "stall_ms_per_step": round(d["stall_ms"] / args.steps, 4),
+            "blocks_in_per_step": d["blocks_in"] / args.steps, "blocks_out_per_step": d["blocks_out"] / args.steps}
+    summary = {}
+    for k, f in forms.items():
+        dd = f["delta"]
+        summary[k] = {"iters_per_s": round(f["iters"], 2), "ms_per_step": round(f["ms"] / args.steps, 4),
+                      "psnr_heldout_db": round(f["psnr"], 3),
+                      "h2d_bytes_per_step": dd["bytes_h2d"] / args.steps,
+                      "stall_ms_per_step": round(dd["stall_ms"] / args.steps, 4),
+                      "demand_hit_rate": round(dd["demand_hits"] / max(dd["demand_blocks"], 1), 5),
+                      "predicted_blocks_per_step": dd["predicted_blocks"] / args.steps,
+                      "readmissions": dd["readmissions"], "writebacks": dd["writebacks"]}
+    gap = forms["fp32_reactive"]["psnr"] - forms["bf16_learned"]["psnr"]
+    out = dict(ms=head["ms"], stages=head["stages"], stats=head["stats"], launches=head["delta"]["kernel_launches"],
+               clocks=head["clocks"], rec=head["rec"], table=tb, cams=cams, W=W, H=H, e2e_ms=e2e_ms,
+               bytes_in=H * W * 3 * 4, link=link, n=n, nc=nc, cache_blocks=cache, setup_s=round(t_setup, 1),
+               host=host, forms=summary, psnr_gap_db=round(gap, 4), predictor_train_s=round(t_train, 1))
+    out["_pred"] = pred
+    return out
 
 
 def cpu_baseline_street(res):
@@ -463,11 +529,13 @@ def main():
     ms_step = res["ms"] / args.steps
     value = world * 1e3 / ms_step
     if street:
-        config = {"workload": "street-100M-1600x900-outofcore-fp32", "n_gaussians": res["n"], "block_size": 4096,
-                  "image": f"{res['W']}x{res['H']}", "global_batch": world, "cameras": res["nc"],
-                  "cache_blocks": res["cache_blocks"], "cache_gb": 24, "host_tier": "pinned FP32 params+m+v",
-                  "prefetch": "exact next batch", "parallelism": f"replicas{world}",
-                  "l2": "per-step state > 126 MB L2, no flush", "setup_s": res["setup_s"]}
+        config = {"workload": "street-100M-1600x900-outofcore-bf16-learned", "n_gaussians": res["n"],
+                  "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
+                  "cameras": res["nc"], "heldout": "every 10th camera", "cache_blocks": res["cache_blocks"],
+                  "cache_gb": 24, "host_tier": "pinned: FP32 mean/scale/rot/opacity/SH-DC, BF16 SH-rest and moments",
+                  "prefetch": "learned (MLP on the last 8 poses), exact culling for the actual batch",
+                  "parallelism": f"replicas{world}", "l2": "per-step state > 126 MB L2, no flush",
+                  "setup_s": res["setup_s"]}
     else:
         config = {"workload": "aerial-2M-1080p-resident-fp32", "n_gaussians": args.n or 2_000_000,
                   "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
@@ -487,6 +555,9 @@ def main():
     }
     if street:
         line["link"] = res["link"]
+        line["forms"] = res["forms"]
+        line["psnr_gap_db"] = res["psnr_gap_db"]
+        line["vs_fp32_reactive"] = round(value / max(res["forms"]["fp32_reactive"]["iters_per_s"], 1e-9), 4)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()

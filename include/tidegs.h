@@ -133,6 +133,10 @@ tgs_status tgs_step(tgs_table* t, const tgs_camera* cams, uint32_t batch, const 
  * policy, without parameter updates).  image_dev: device, H x W x 3. */
 tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, void* stream);
 
+/* Changes prefetch_mode (0 reactive, 1 exact next batch, 2 learned) between
+ * steps; a pending prefetch is kept and used if it matches the next batch. */
+tgs_status tgs_set_prefetch_mode(tgs_table* t, uint32_t mode);
+
 /* Waits for all queued work of the table. */
 tgs_status tgs_sync(tgs_table* t);
 

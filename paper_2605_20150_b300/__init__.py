@@ -64,6 +64,7 @@ _SIGS = {
                                   _VP, ctypes.POINTER(_F)]),
     "tgs_render": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_camera), _VP, _VP]),
     "tgs_sync": (ctypes.c_int32, [_VP]),
+    "tgs_set_prefetch_mode": (ctypes.c_int32, [_VP, _U32]),
     "tgs_get_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_set_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_state": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP]),
@@ -217,6 +218,9 @@ class TideTable:
 
     def sync(self):
         _check(load().tgs_sync(self.h))
+
+    def set_prefetch_mode(self, mode):
+        _check(load().tgs_set_prefetch_mode(self.h, mode))
 
     def set_params(self, params):
         """params: host numpy [n, 59] (original row order) or a CUDA tensor (copied to host)."""

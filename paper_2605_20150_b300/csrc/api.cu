@@ -160,6 +160,13 @@ tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, voi
   });
 }
 
+tgs_status tgs_set_prefetch_mode(tgs_table* t, uint32_t mode) {
+  return guard([&] {
+    TGS_CHECK(t && mode <= 2, TGS_ERR_INVALID, "tgs_set_prefetch_mode: bad argument");
+    t->t.cfg.prefetch_mode = mode;
+  });
+}
+
 tgs_status tgs_sync(tgs_table* t) {
   return guard([&] {
     TGS_CHECK(t, TGS_ERR_INVALID, "tgs_sync: null table");

@@ -580,7 +580,8 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     stats.steps++;
   }
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
-  if (user) TGS_CUDA(cudaStreamWaitEvent(user, ev_comp, 0));
+  // the caller's stream (NULL: the legacy default stream) waits for this step
+  TGS_CUDA(cudaStreamWaitEvent(user, ev_comp, 0));
   last_cams = p.cams;
   last_render = p.render_blocks;
   last_splus = p.s_plus;

@@ -80,3 +80,20 @@ def test_cold_restart_drops_moments(orc, tgs):
     assert not m[out].any() and not v[out].any()
     assert m[~out].any()
     tab.close()
+
+
+def test_render_is_ordered_on_the_default_stream(tgs):
+    """tgs_render on the caller's (legacy default) stream: reading the image on
+    that stream without a device-wide synchronisation sees the finished render."""
+    import torch
+    cfg = scenes.small_cube_config()
+    tab = tgs.TideTable(cfg["params"], block_size=250, max_batch=1, max_width=256, max_height=256)
+    ref = torch.empty(256, 256, 3, device="cuda")
+    tab.render(cfg["cams"][0], ref)
+    torch.cuda.synchronize()
+    ref_h = ref.cpu().numpy()
+    for _ in range(3):
+        img = torch.full((256, 256, 3), -1.0, device="cuda")
+        tab.render(cfg["cams"][0], img)
+        assert np.array_equal(img.cpu().numpy(), ref_h)  # .cpu() runs on the default stream
+    tab.close()
