@@ -79,7 +79,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&ctl, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb})
+  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb, &ev_snap})
     TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   TGS_CUDA(cudaEventCreate(&ev_stall_a));
   TGS_CUDA(cudaEventCreate(&ev_stall_b));
@@ -112,6 +112,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   // ---- device cache and state
   dalloc(pool, n_slots * rec_floats);
   dalloc(spheres, K);
+  dalloc(spheres_snap, K);
   dalloc(ages, K);
   dalloc(block_step, K);
   dalloc(dirty_dev, n_slots);
@@ -216,6 +217,9 @@ void Table::init_spheres() {
     block_bounds(render_list((uint32_t)m), nullptr, spheres, comp);
     TGS_CUDA(cudaStreamSynchronize(comp));
   }
+  TGS_CUDA(cudaMemcpyAsync(spheres_snap, spheres, K * sizeof(float4), cudaMemcpyDeviceToDevice, comp));
+  TGS_CUDA(cudaEventRecord(ev_snap, comp));
+  TGS_CUDA(cudaStreamSynchronize(comp));
 }
 
 // Replaces every parameter (rows in the caller's original order), zeroes the
@@ -247,7 +251,7 @@ void Table::destroy() {
   if (d2h) cudaStreamSynchronize(d2h);
   if (ctl) cudaStreamSynchronize(ctl);
   for (auto& cs : cams) cam_state_free(cs);
-  void* dev[] = {pool, spheres, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
+  void* dev[] = {pool, spheres, spheres_snap, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
                  kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
                  rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, grad_local,
                  loss_dev};
@@ -257,7 +261,7 @@ void Table::destroy() {
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb})
+  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap})
     if (e) cudaEventDestroy(e);
   for (cudaStream_t s : {comp, h2d, d2h, ctl})
     if (s) cudaStreamDestroy(s);
@@ -266,7 +270,7 @@ void Table::destroy() {
 // Stage 1 + Algorithm 1 for a batch, enqueued on the control stream: cull,
 // select R_next, derive S+ / S- and the render list; their counts are copied
 // back asynchronously.  prepare_finish() reads the lists and assigns slots.
-void Table::prepare_enqueue(const tgs_camera* cs, uint32_t J, Prepared& out) {
+void Table::prepare_enqueue(const tgs_camera* cs, uint32_t J, Prepared& out, bool own_batch) {
   TGS_CHECK(J >= 1 && J <= cfg.max_batch, TGS_ERR_INVALID, "batch size out of range");
   for (uint32_t j = 0; j < J; ++j) {
     TGS_CHECK(cs[j].width == cs[0].width && cs[j].height == cs[0].height, TGS_ERR_INVALID,
@@ -279,10 +283,18 @@ void Table::prepare_enqueue(const tgs_camera* cs, uint32_t J, Prepared& out) {
   }
   out = Prepared();
   out.cams.assign(cs, cs + J);
-  // spheres reflect every step already enqueued on the compute stream
-  TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+  // Batch t is culled with the bounds refreshed through step t-2: a batch
+  // selected at its own step reads the snapshot taken when step t-1 started;
+  // the next batch selected at the start of step t reads the bounds after
+  // step t-1 (the control stream waits for that step, the host does not).
   TGS_CUDA(cudaMemcpyAsync(planes_dev, planes_host, J * sizeof(Planes), cudaMemcpyHostToDevice, ctl));
-  cull_blocks(spheres, K, planes_dev, (int)J, kvis, kvis_union, ctl);
+  if (own_batch) {
+    TGS_CUDA(cudaStreamWaitEvent(ctl, ev_snap, 0));
+    cull_blocks(spheres_snap, K, planes_dev, (int)J, kvis, kvis_union, ctl);
+  } else {
+    TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+    cull_blocks(spheres, K, planes_dev, (int)J, kvis, kvis_union, ctl);
+  }
   select_enqueue(J, out, true);
 }
 
@@ -518,6 +530,12 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   TGS_CUDA(cudaStreamWaitEvent(comp, ev_h2d, 0));
   TGS_CUDA(cudaEventRecord(ev_stall_b, comp));
   stall_pending = true;
+  if (backward) {
+    // the bounds as this step starts: the next own-batch cull reads them while
+    // this step refreshes the live copy
+    TGS_CUDA(cudaMemcpyAsync(spheres_snap, spheres, K * sizeof(float4), cudaMemcpyDeviceToDevice, comp));
+    TGS_CUDA(cudaEventRecord(ev_snap, comp));
+  }
   for (uint32_t j = 0; j < n_items; ++j) {
     uint32_t b = p.render_blocks[j];
     rl_host[j] = p.render_slots[j];
@@ -601,7 +619,7 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   if (!(prep.valid && same_cams(prep.cams, cs, J))) {
     // reactive path: select and stream this batch's working set now
     Prepared p;
-    prepare_enqueue(cs, J, p);
+    prepare_enqueue(cs, J, p, true);
     prepare_finish(p);
     issue_early(p);
     issue_evictions_and_late(p);
@@ -618,7 +636,7 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   const bool learned = cfg.prefetch_mode == 2 && predictor != nullptr;
   // Algorithm 1 for batch t+1 runs on the control stream while batch t is
   // enqueued; it sees the bounds as of the start of step t
-  if (prefetch) prepare_enqueue(next, nJ, nxt);
+  if (prefetch) prepare_enqueue(next, nJ, nxt, false);
   if (learned) prepare_enqueue_predicted(nxt);
   compute(cur, targets_dev, targets_host, user, true, nullptr);
   if (prefetch || learned) {
@@ -638,7 +656,7 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
 
 void Table::render(const tgs_camera& cam, float* image_dev, cudaStream_t user) {
   Prepared p;
-  prepare_enqueue(&cam, 1, p);
+  prepare_enqueue(&cam, 1, p, true);
   prepare_finish(p);
   issue_early(p);
   issue_evictions_and_late(p);

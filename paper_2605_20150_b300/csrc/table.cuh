@@ -46,6 +46,7 @@ struct Table {
   // device state
   float* pool = nullptr;
   float4* spheres = nullptr;
+  float4* spheres_snap = nullptr;  // bounds as of the start of the latest compute
   uint32_t* ages = nullptr;
   uint32_t* block_step = nullptr;
   uint8_t* dirty_dev = nullptr;
@@ -79,6 +80,7 @@ struct Table {
   std::vector<uint8_t> ever_loaded;      // K: for the re-admission counter
   std::vector<uint8_t> wb_pending;       // K: write-back to the host tier issued, not yet waited on
   cudaEvent_t ev_wb = nullptr;           // recorded after each write-back batch on d2h
+  cudaEvent_t ev_snap = nullptr;         // recorded after the bounds snapshot on comp
 
   // last computed batch (for the debug getters)
   std::vector<tgs_camera> last_cams;
@@ -107,7 +109,7 @@ struct Table {
   void fill_host(const float* params);
   void init_spheres();
   void set_params(const float* params);
-  void prepare_enqueue(const tgs_camera* cams, uint32_t J, Prepared& out);
+  void prepare_enqueue(const tgs_camera* cams, uint32_t J, Prepared& out, bool own_batch);
   void prepare_enqueue_predicted(Prepared& out);
   void select_enqueue(uint32_t J, Prepared& out, bool accessed);
   void cull_only(const tgs_camera* cams, uint32_t J, uint8_t* vis_host);

@@ -240,31 +240,58 @@ def _t_mix64(z):
     return z ^ _t_lsr(z, 31)
 
 
+def t_u64_at(seed, stream, idx):
+    """int64 tensor holding the bits of draws idx (an int64 tensor) of a stream."""
+    key = int(np.int64(stream_key(seed, stream).astype(np.int64)))
+    gamma = int(np.int64(GAMMA.astype(np.int64)))
+    return _t_mix64((idx + 1) * gamma + key)
+
+
 def t_u64(seed, stream, start, count, device):
     """int64 tensor holding the bits of draws [start, start+count) of a stream."""
     import torch
-    key = int(np.int64(stream_key(seed, stream).astype(np.int64)))
-    gamma = int(np.int64(GAMMA.astype(np.int64)))
-    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
-    return _t_mix64(idx * gamma + key)
+    return t_u64_at(seed, stream, torch.arange(start, start + count, dtype=torch.int64, device=device))
+
+
+def _t_unit(bits):
+    import torch
+    return _t_lsr(bits, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def t_uniform_at(seed, stream, idx, lo=0.0, hi=1.0):
+    return lo + (hi - lo) * _t_unit(t_u64_at(seed, stream, idx))
+
+
+def t_normal_at(seed, stream, idx, mean=0.0, std=1.0):
+    """Box-Muller normal of element idx: draws 2 idx and 2 idx + 1."""
+    u1 = 1.0 - _t_unit(t_u64_at(seed, stream, 2 * idx))
+    u2 = _t_unit(t_u64_at(seed, stream, 2 * idx + 1))
+    return mean + std * torch_sqrt_log_cos(u1, u2)
+
+
+def torch_sqrt_log_cos(u1, u2):
+    import torch
+    return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
 
 
 def t_uniform(seed, stream, count, lo=0.0, hi=1.0, start=0, device="cuda"):
-    import torch
-    x = _t_lsr(t_u64(seed, stream, start, count, device), 11).to(torch.float64) * (1.0 / 9007199254740992.0)
-    return lo + (hi - lo) * x
+    return lo + (hi - lo) * _t_unit(t_u64(seed, stream, start, count, device))
 
 
 def t_normal(seed, stream, count, mean=0.0, std=1.0, start=0, device="cuda"):
+    u = _t_unit(t_u64(seed, stream, 2 * start, 2 * count, device))
+    return mean + std * torch_sqrt_log_cos(1.0 - u[0::2], u[1::2])
+
+
+def _cols_at(seed, stream, rows, ncol, fn, **kw):
+    """[len(rows), ncol] draws of elements ncol * row + c of a stream."""
     import torch
-    u = _t_lsr(t_u64(seed, stream, 2 * start, 2 * count, device), 11).to(torch.float64) * (1.0 / 9007199254740992.0)
-    u1 = 1.0 - u[0::2]
-    u2 = u[1::2]
-    return mean + std * torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+    e = rows[:, None] * ncol + torch.arange(ncol, dtype=torch.int64, device=rows.device)[None, :]
+    return fn(seed, stream, e.reshape(-1), **kw).reshape(len(rows), ncol)
 
 
 def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_width=20.0, ground_frac=0.5,
-                 device="cuda", chunk=1 << 24):
+                 device="cuda", chunk=1 << 24, near=None):
     """Synthetic street grid (world z up) of n Gaussians as a float32 torch
     tensor [n, 59] on `device`: roads every 100 m over a side x side square,
     a ground layer (ground_frac of the Gaussians, uniform over the square) and
@@ -272,7 +299,12 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
     block, Gaussians uniform over the facade area).  Log-scales log(spacing/2)
     + N(0, 0.3) with spacing the mean distance between neighbours; opacity
     logit N(2, 0.5); SH DC from a smooth field plus a per-block tint, SH rest
-    N(0, 0.05).  Generated in chunks of `chunk` rows."""
+    N(0, 0.05).  Generated in chunks of `chunk` rows; every value is a
+    function of its row index only.
+
+    near=(centre xyz, radius): return only the rows whose mean lies within
+    the radius of the centre (bit-identical to those rows of the full table),
+    as (rows [m, 59], row indices [m] int64, spacing)."""
     import torch
     nb = int(side // road_every)
     heights = t_uniform(seed, 40, nb * nb, 10.0, 60.0, device=device)
@@ -281,19 +313,19 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
     facade_area = (4 * inner * heights).sum().item()
     ground_area = side * side
     n_ground = int(n * ground_frac)
-    n_fac = n - n_ground
     spacing = math.sqrt((ground_area + facade_area) / n)
-    out = torch.empty((n, D), dtype=torch.float32, device=device)
+    out = torch.empty((n, D), dtype=torch.float32, device=device) if near is None else []
+    kept = []
     # facade sampling: block by cumulative facade area
     cdf = torch.cumsum(4 * inner * heights, 0)
     cdf = cdf / cdf[-1]
     for a in range(0, n, chunk):
         m = min(chunk, n - a)
         i = torch.arange(a, a + m, device=device)
-        u1 = t_uniform(seed, 42, m, start=a, device=device)
-        u2 = t_uniform(seed, 43, m, start=a, device=device)
-        u3 = t_uniform(seed, 44, m, start=a, device=device)
-        u4 = t_uniform(seed, 45, m, start=a, device=device)
+        u1 = t_uniform_at(seed, 42, i)
+        u2 = t_uniform_at(seed, 43, i)
+        u3 = t_uniform_at(seed, 44, i)
+        u4 = t_uniform_at(seed, 45, i)
         pos = torch.empty((m, 3), dtype=torch.float64, device=device)
         g = i < n_ground
         pos[g, 0] = u1[g] * side - side / 2
@@ -313,22 +345,37 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
         pos[f, 0] = fx
         pos[f, 1] = fy
         pos[f, 2] = u2[f] * h
-        row = out[a:a + m]
+        if near is not None:
+            c = torch.tensor(np.asarray(near[0], np.float64), device=device)
+            sel = ((pos.to(torch.float32).to(torch.float64) - c) ** 2).sum(1) < float(near[1]) ** 2
+            i, pos = i[sel], pos[sel]
+            m = len(i)
+            if m == 0:
+                continue
+        row = torch.empty((m, D), dtype=torch.float32, device=device)
         row[:, 0:3] = pos.to(torch.float32)
-        row[:, 3:6] = (math.log(0.5 * spacing) + t_normal(seed, 46, 3 * m, 0.0, 0.3, start=3 * a, device=device)
-                       ).reshape(m, 3).to(torch.float32)
-        q = t_normal(seed, 47, 4 * m, start=4 * a, device=device).reshape(m, 4)
+        row[:, 3:6] = (math.log(0.5 * spacing) + _cols_at(seed, 46, i, 3, t_normal_at, std=0.3)).to(torch.float32)
+        q = _cols_at(seed, 47, i, 4, t_normal_at)
         row[:, 6:10] = (q / q.norm(dim=1, keepdim=True)).to(torch.float32)
-        row[:, 10] = t_normal(seed, 48, m, 2.0, 0.5, start=a, device=device).to(torch.float32)
-        rest = t_normal(seed, 49, 48 * m, 0.0, 0.05, start=48 * a, device=device).reshape(m, 16, 3)
+        row[:, 10] = t_normal_at(seed, 48, i, 2.0, 0.5).to(torch.float32)
+        rest = _cols_at(seed, 49, i, 48, t_normal_at, std=0.05).reshape(m, 16, 3)
         cell = ((pos[:, 0] + side / 2) // road_every).clamp(0, nb - 1).long() * nb + \
             ((pos[:, 1] + side / 2) // road_every).clamp(0, nb - 1).long()
         col = torch.stack([0.5 + 0.25 * torch.sin(pos[:, 0] / 23.0 + 0.4 * c) * torch.cos(pos[:, 1] / 31.0 - 0.6 * c)
                            + 0.1 * torch.sin(pos[:, 2] / 7.0 + c) for c in range(3)], 1) + tint[cell]
         rest[:, 0, :] = (col - 0.5) * 3.5
         row[:, 11:59] = rest.reshape(m, 48).to(torch.float32)
-        del pos, rest, col, q
-    return out, spacing
+        if near is None:
+            out[a:a + m] = row
+        else:
+            out.append(row)
+            kept.append(i)
+        del pos, rest, col, q, row
+    if near is None:
+        return out, spacing
+    if not out:
+        return torch.zeros((0, D), dtype=torch.float32, device=device), torch.zeros(0, dtype=torch.int64), spacing
+    return torch.cat(out), torch.cat(kept), spacing
 
 
 def street_drive_cameras(n_cams=500, seed=1003, side=4000.0, road_every=100.0, height=1.5, step=2.0,
