@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--workload", default="street100m", choices=["aerial2m", "street100m"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--cams", type=int, default=None)
+    ap.add_argument("--cache-gb", type=float, default=24.0, help="HBM working-set cache cap (street workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -272,7 +273,7 @@ def run_street(args, rank, world, local):
     del gt
     torch.cuda.empty_cache()
     W, H = cams[0]["width"], cams[0]["height"]
-    cache = int(24e9 // (4096 * 708))
+    cache = int(args.cache_gb * 1e9 // (4096 * 708))
     base = dict(block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache, spare_slots=512,
                 moments_policy=0, loss=0)
     table = tgs.TideTable(host, prefetch_mode=0, **base)
@@ -311,10 +312,12 @@ def run_street(args, rank, world, local):
         clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed:" + label)
         e0.record(s)
         for k in range(args.warmup, args.warmup + args.steps):
             one(k)
         e1.record(s)
+        torch.cuda.nvtx.range_pop()
         tab.sync()
         torch.cuda.synchronize()
         clocks = clk.stop()
@@ -366,7 +369,7 @@ def run_street(args, rank, world, local):
     t1 = time.perf_counter()
     for k in range(n_e2e):
         i = k % host_np.shape[0]
-        tb.step([cams[i]], host_np[i:i + 1], next_cams=[cams[i + 1]], want_loss=True)
+        tb.step([cams[i]], host_np[i:i + 1], next_cams=[cams[(i + 1) % nc]], want_loss=True)
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
     d = head["delta"]
@@ -584,7 +587,7 @@ def main():
         config = {"workload": "street-100M-1600x900-outofcore-bf16-learned", "n_gaussians": res["n"],
                   "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
                   "cameras": res["nc"], "heldout": "every 10th camera", "cache_blocks": res["cache_blocks"],
-                  "cache_gb": 24, "host_tier": "pinned: FP32 mean/scale/rot/opacity/SH-DC, BF16 SH-rest and moments",
+                  "cache_gb": args.cache_gb, "host_tier": "pinned: FP32 mean/scale/rot/opacity/SH-DC, BF16 SH-rest and moments",
                   "prefetch": "learned (MLP on the last 8 poses), exact culling for the actual batch",
                   "parallelism": f"replicas{world}", "l2": "per-step state > 126 MB L2, no flush",
                   "setup_s": res["setup_s"]}

@@ -89,6 +89,11 @@ typedef struct tgs_config {
   uint32_t stochastic_round; /* BF16 stores of Adam: 1 stochastic rounding (counter hash
                               of seed, Gaussian id, field, step), 0 round to nearest */
   uint32_t seed;
+  uint64_t pair_capacity;  /* initial (tile, Gaussian) pair capacity per camera; 0 = the larger
+                              of 2 x the render-list capacity and 16 x max_width x max_height.  A render whose pairs exceed it is
+                              completed on the device without the excess, its step's update
+                              is skipped, and the capacity grows once the host sees the
+                              count (tgs_stats.pair_overflows / dropped_steps). */
 } tgs_config;
 
 void tgs_default_config(tgs_config* cfg);
@@ -200,6 +205,11 @@ typedef struct tgs_stats {
   uint64_t demand_hits;     /* ... of those already resident before the batch's own selection */
   uint64_t predicted_blocks; /* blocks streamed in on a prediction (learned prefetch) */
   uint64_t last_pairs, last_visible, last_render_blocks;
+  /* Tile/Gaussian pair capacity: renders whose pairs exceeded it (the
+   * capacity then grows), and training steps whose update was skipped
+   * because a render of theirs, or of an earlier step not yet seen by the
+   * host, overflowed. */
+  uint64_t pair_overflows, dropped_steps;
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
 

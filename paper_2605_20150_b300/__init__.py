@@ -40,7 +40,8 @@ class tgs_config(ctypes.Structure):
                 ("max_height", ctypes.c_uint32), ("quota", ctypes.c_uint32), ("lambda_", ctypes.c_float),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("cull_margin_px", ctypes.c_float), ("bg", ctypes.c_float * 3), ("loss", ctypes.c_uint32),
-                ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32)]
+                ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32),
+                ("pair_capacity", ctypes.c_uint64)]
 
 
 class tgs_stats(ctypes.Structure):
@@ -50,7 +51,8 @@ class tgs_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("stall_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
                 ("d2h_ms", ctypes.c_double), ("demand_blocks", ctypes.c_uint64), ("demand_hits", ctypes.c_uint64),
                 ("predicted_blocks", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
-                ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64)]
+                ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64),
+                ("pair_overflows", ctypes.c_uint64), ("dropped_steps", ctypes.c_uint64)]
 
 
 _VP = ctypes.c_void_p

@@ -172,6 +172,7 @@ tgs_status tgs_sync(tgs_table* t) {
     TGS_CHECK(t, TGS_ERR_INVALID, "tgs_sync: null table");
     for (cudaStream_t s : {t->t.comp, t->t.h2d, t->t.d2h, t->t.ctl}) TGS_CUDA(cudaStreamSynchronize(s));
     t->t.collect_stall();
+    t->t.check_overflow(true);
   });
 }
 
@@ -330,8 +331,8 @@ static void camera_record(CamState& cs, const std::vector<uint32_t>& blocks, uin
       }
     }
   }
-  if (pair_vals && cs.n_pairs)
-    TGS_CUDA(cudaMemcpy(pair_vals, cs.pvals, cs.n_pairs * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  const uint64_t np = std::min(cs.n_pairs, cs.cap_pairs);
+  if (pair_vals && np) TGS_CUDA(cudaMemcpy(pair_vals, cs.pvals, np * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   if (ranges) TGS_CUDA(cudaMemcpy(ranges, cs.ranges, tiles * sizeof(uint2), cudaMemcpyDeviceToHost));
   if (image && image_dev) TGS_CUDA(cudaMemcpy(image, image_dev, pix * 3 * sizeof(float), cudaMemcpyDeviceToHost));
   if (t_final) TGS_CUDA(cudaMemcpy(t_final, cs.t_final, pix * sizeof(float), cudaMemcpyDeviceToHost));
@@ -352,6 +353,7 @@ tgs_status tgs_get_camera_record(tgs_table* t, uint32_t j, uint64_t* n_gauss, ui
     Table& T = t->t;
     TGS_CHECK(j < T.last_cams.size(), TGS_ERR_INVALID, "camera index out of range of the last batch");
     TGS_CUDA(cudaStreamSynchronize(T.comp));
+    cam_state_counts(T.cams[j], true);
     const uint64_t pix = (uint64_t)T.cams[j].W * T.cams[j].H;
     camera_record(T.cams[j], T.last_render, T.B, T.N, T.images + (uint64_t)j * pix * 3, n_gauss, n_pairs, ids,
                   splat, rect, pair_vals, ranges, image, t_final, n_last, grad2d);
@@ -363,6 +365,13 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out) {
     TGS_CHECK(t && out, TGS_ERR_INVALID, "tgs_get_stats: null argument");
     t->t.collect_stall();
     t->t.copy_timer.collect();
+    t->t.check_overflow(true);
+    if (!t->t.last_cams.empty()) {
+      CamState& cs = t->t.cams[t->t.last_cams.size() - 1];
+      cam_state_counts(cs, true);
+      t->t.stats.last_pairs = cs.n_pairs;
+      t->t.stats.last_visible = cs.n_vis;
+    }
     *out = t->t.stats;
     out->kernel_launches = g_launches;
     out->h2d_ms = t->t.copy_timer.ms[0];
@@ -508,6 +517,15 @@ tgs_status tgs_raster_forward(tgs_raster* r, const float* params_dev, uint64_t n
     float bg[3] = {0.f, 0.f, 0.f};
     if (bg3) std::memcpy(bg, bg3, sizeof(bg));
     render_forward(rl, make_devcam(*cam), bg, r->r.cs, image_dev, nullptr, nullptr, s);
+    // the image is returned complete: after a pair overflow the buffers grow
+    // and the render runs again
+    cam_state_counts(r->r.cs, true);
+    if (r->r.cs.overflow) {
+      cam_state_grow_pairs(r->r.cs, r->r.cs.pairs_needed, s);
+      TGS_CUDA(cudaMemset(r->r.cs.counters + 2, 0, 2 * sizeof(uint32_t)));
+      r->r.cs.overflow = false;
+      render_forward(rl, make_devcam(*cam), bg, r->r.cs, image_dev, nullptr, nullptr, s);
+    }
   });
 }
 

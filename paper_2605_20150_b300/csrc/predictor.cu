@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "predictor.cuh"
+#include "sort.cuh"
 
 namespace tgs {
 namespace {
@@ -74,7 +75,9 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
 __global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ P, const __nv_bfloat16* __restrict__ w2t,
                                                 const float* __restrict__ pterm, const float* __restrict__ feat,
                                                 uint64_t M, float* __restrict__ z3, __nv_bfloat16* __restrict__ h1g,
-                                                float* __restrict__ h2g) {
+                                                float* __restrict__ h2g, const uint32_t* __restrict__ rows_dev) {
+  // rows_dev (device, may be null): only the first *rows_dev rows are wanted
+  if (rows_dev && (uint64_t)blockIdx.x * MLP_ROWS_PER_CTA >= *rows_dev) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* w2s = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* h1s = w2s + MLP_H * W2S;
@@ -334,6 +337,58 @@ __global__ void k_mlp_threshold(const float* __restrict__ z3, uint64_t K, uint32
   if ((threadIdx.x & 31) == 0 && (k >> 5) < words) bits[k >> 5] = wd;
 }
 
+// Candidates of a prediction: blocks whose sphere comes within lim of the
+// current camera centre, lim = the distance of the frustum's far corners plus
+// how far the camera can travel over the predicted horizons; the others
+// cannot enter the frustum in that time.
+__global__ void k_mlp_cand(const float4* __restrict__ sph, uint64_t K, DevCam c, float lim,
+                           uint32_t* __restrict__ flag) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const float4 s = sph[k];
+  float cx = c.R[0] * s.x + c.R[1] * s.y + c.R[2] * s.z + c.t[0];
+  float cy = c.R[3] * s.x + c.R[4] * s.y + c.R[5] * s.z + c.t[1];
+  float cz = c.R[6] * s.x + c.R[7] * s.y + c.R[8] * s.z + c.t[2];
+  flag[k] = sqrtf(cx * cx + cy * cy + cz * cz) - s.w <= lim ? 1u : 0u;
+}
+
+// Features of the candidates, packed in block order at rows pos[k].
+__global__ void k_mlp_feat_cand(const float4* __restrict__ sph, uint64_t K, const uint32_t* __restrict__ flag,
+                                const uint32_t* __restrict__ pos, DevCam c, float zf, float* __restrict__ feat,
+                                uint32_t* __restrict__ cid) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K || !flag[k]) return;
+  const uint32_t r = pos[k];
+  cid[r] = (uint32_t)k;
+  float4 s = sph[k];
+  float cx = c.R[0] * s.x + c.R[1] * s.y + c.R[2] * s.z + c.t[0];
+  float cy = c.R[3] * s.x + c.R[4] * s.y + c.R[5] * s.z + c.t[1];
+  float cz = c.R[6] * s.x + c.R[7] * s.y + c.R[8] * s.z + c.t[2];
+  float d = sqrtf(cx * cx + cy * cy + cz * cz);
+  float iz = 1.f / zf;
+  float* o = feat + 8 * (uint64_t)r;
+  o[0] = cx * iz;
+  o[1] = cy * iz;
+  o[2] = cz * iz;
+  o[3] = s.w * iz;
+  o[4] = d * iz;
+  o[5] = s.w / fmaxf(d, s.w);
+  o[6] = 0.f;
+  o[7] = 0.f;
+}
+
+__global__ void k_mlp_threshold_cand(const float* __restrict__ z3, const uint32_t* __restrict__ count,
+                                     const uint32_t* __restrict__ cid, uint32_t mask, float zthr,
+                                     uint32_t* __restrict__ bits) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= *count) return;
+  bool vis = false;
+#pragma unroll
+  for (int h = 0; h < MLP_OUT; ++h)
+    if ((mask >> h & 1u) && z3[r * MLP_OUT + h] > zthr) vis = true;
+  if (vis) atomicOr(bits + (cid[r] >> 5), 1u << (cid[r] & 31));
+}
+
 size_t fwd_smem_bytes() {
   return (size_t)MLP_H * W2S * 2 + (size_t)MLP_ROWS_PER_CTA * W2S * 2 +
          sizeof(float) * (MLP_NFEAT * MLP_H + MLP_H + MLP_H + MLP_H * MLP_OUT + 4 + MLP_ROWS_PER_CTA * 8);
@@ -361,6 +416,13 @@ void mlp_alloc(Mlp& m, uint64_t max_rows, uint32_t seed) {
   TGS_CUDA(cudaMalloc(&m.dz3, R * MLP_OUT * sizeof(float)));
   TGS_CUDA(cudaMalloc(&m.loss, sizeof(float)));
   TGS_CUDA(cudaMallocHost(&m.loss_host, sizeof(float)));
+  TGS_CUDA(cudaMalloc(&m.cflag, R * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&m.cpos, R * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&m.cid, R * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&m.ccount, 4 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&m.cscratch, scan_scratch_bytes(R)));
+  // rows past a candidate count are computed and ignored: keep them finite
+  TGS_CUDA(cudaMemset(m.feat, 0, R * 8 * sizeof(float)));
   // initial weights: N(0, 1/sqrt(fan_in)), zero biases (seeded)
   std::vector<float> h(MLP_NPARAM, 0.f);
   std::mt19937_64 rng(seed);
@@ -381,7 +443,7 @@ void mlp_alloc(Mlp& m, uint64_t max_rows, uint32_t seed) {
 
 void mlp_free(Mlp& m) {
   void* p[] = {m.params, m.grads, m.m, m.v, m.w2t, m.w2r, m.pose, m.pterm, m.feat, m.h1, m.h2, m.z3, m.dh2, m.dh1,
-               m.dz3, m.loss};
+               m.dz3, m.loss, m.cflag, m.cpos, m.cid, m.ccount, m.cscratch};
   for (void* x : p)
     if (x) cudaFree(x);
   if (m.loss_host) cudaFreeHost(m.loss_host);
@@ -431,7 +493,7 @@ void mlp_forward(Mlp& m, const float4* spheres, uint64_t K, const tgs_camera* hi
   k_mlp_pose<<<1, MLP_H, 0, s>>>(m.params, pv, m.pose, m.pterm);
   TGS_LAUNCHED();
   k_mlp_fwd<<<(unsigned)(M / MLP_ROWS_PER_CTA), 128, fwd_smem_bytes(), s>>>(
-      m.params, m.w2t, m.pterm, m.feat, M, m.z3, keep ? m.h1 : nullptr, keep ? m.h2 : nullptr);
+      m.params, m.w2t, m.pterm, m.feat, M, m.z3, keep ? m.h1 : nullptr, keep ? m.h2 : nullptr, nullptr);
   TGS_LAUNCHED();
   if (logits && logits != m.z3)
     TGS_CUDA(cudaMemcpyAsync(logits, m.z3, K * MLP_OUT * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -479,6 +541,33 @@ float mlp_train_step(Mlp& m, uint64_t K, const float* labels, float pw, float lr
   TGS_CUDA(cudaMemcpyAsync(m.loss_host, m.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
   TGS_CUDA(cudaStreamSynchronize(s));
   return *m.loss_host;
+}
+
+void mlp_predict_near(Mlp& m, const float4* spheres, uint64_t K, const tgs_camera* hist, float reach, uint32_t mask,
+                      float thr, uint32_t* bits, cudaStream_t s) {
+  TGS_CHECK(K >= 1 && K <= m.max_rows, TGS_ERR_CAPACITY, "predictor rows exceed the allocated maximum");
+  const uint64_t M = (K + MLP_ROWS_PER_CTA - 1) / MLP_ROWS_PER_CTA * MLP_ROWS_PER_CTA;
+  const tgs_camera& c = hist[MLP_HIST - 1];
+  DevCam dc = make_devcam(c);
+  PoseVec pv;
+  mlp_pose_host(hist, pv.v);
+  // the frustum lies inside the ball through its far corners
+  const double tx = 0.5 * c.width / c.fx, ty = 0.5 * c.height / c.fy;
+  const float lim = (float)(c.zfar * std::sqrt(1.0 + tx * tx + ty * ty)) + reach;
+  k_mlp_cand<<<div_up(K, 256), 256, 0, s>>>(spheres, K, dc, lim, m.cflag);
+  TGS_LAUNCHED();
+  exclusive_scan_u32(m.cflag, m.cpos, m.ccount, K, m.cscratch, s);
+  k_mlp_feat_cand<<<div_up(K, 256), 256, 0, s>>>(spheres, K, m.cflag, m.cpos, dc, c.zfar, m.feat, m.cid);
+  TGS_LAUNCHED();
+  k_mlp_pose<<<1, MLP_H, 0, s>>>(m.params, pv, m.pose, m.pterm);
+  TGS_LAUNCHED();
+  k_mlp_fwd<<<(unsigned)(M / MLP_ROWS_PER_CTA), 128, fwd_smem_bytes(), s>>>(m.params, m.w2t, m.pterm, m.feat, M, m.z3,
+                                                                            nullptr, nullptr, m.ccount);
+  TGS_LAUNCHED();
+  const float zthr = std::log(thr / (1.f - thr));
+  TGS_CUDA(cudaMemsetAsync(bits, 0, (K + 31) / 32 * sizeof(uint32_t), s));
+  k_mlp_threshold_cand<<<div_up(K, 256), 256, 0, s>>>(m.z3, m.ccount, m.cid, mask, zthr, bits);
+  TGS_LAUNCHED();
 }
 
 void mlp_threshold(const float* logits, uint64_t K, uint32_t mask, float thr, uint32_t* bits, cudaStream_t s) {

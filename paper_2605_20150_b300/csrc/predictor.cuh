@@ -43,6 +43,11 @@ struct Mlp {
   float* dz3 = nullptr;          // rows x 4
   float* loss = nullptr;         // device scalar
   float* loss_host = nullptr;    // pinned
+  uint32_t* cflag = nullptr;     // candidate prediction: per-block flag,
+  uint32_t* cpos = nullptr;      //   packed row,
+  uint32_t* cid = nullptr;       //   block of each row,
+  uint32_t* ccount = nullptr;    //   device count
+  void* cscratch = nullptr;
   uint32_t step = 0;
 };
 
@@ -62,5 +67,12 @@ float mlp_train_step(Mlp& m, uint64_t K, const float* labels, float pos_weight, 
 // visibility bits (words of 32 blocks) of blocks whose predicted probability
 // for any horizon in `mask` exceeds thr.
 void mlp_threshold(const float* logits, uint64_t K, uint32_t mask, float thr, uint32_t* bits, cudaStream_t s);
+// Prediction over the candidate blocks only: blocks whose sphere comes within
+// reach of the ball through the far corners of the current camera's frustum
+// (hist[7]) are packed, run through the
+// network and thresholded (probability > thr for a horizon in mask) into
+// bits (zeroed here); every other block is predicted invisible.
+void mlp_predict_near(Mlp& m, const float4* spheres, uint64_t K, const tgs_camera* hist, float reach, uint32_t mask,
+                      float thr, uint32_t* bits, cudaStream_t s);
 
 }  // namespace tgs

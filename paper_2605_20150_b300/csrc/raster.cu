@@ -256,34 +256,105 @@ __global__ void k_compact_visible(uint64_t V, const uint32_t* __restrict__ ntile
   dvals[q] = (uint32_t)i;
 }
 
-__global__ void k_gather_counts(uint64_t nv, const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ ntiles,
-                                uint32_t* __restrict__ cnt) {
+// The counts below (visible Gaussians nv, pairs np) are read from device
+// memory, written by the scans that precede them on the stream.
+__global__ void k_gather_counts(const uint32_t* __restrict__ nv_dev, const uint32_t* __restrict__ dvals,
+                                const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cnt) {
   uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < nv) cnt[s] = ntiles[dvals[s]];
+  if (s < *nv_dev) cnt[s] = ntiles[dvals[s]];
 }
 
-__global__ void k_emit_pairs(uint64_t nv, const uint32_t* __restrict__ dvals, const ushort4* __restrict__ rect,
-                             const uint32_t* __restrict__ off, int TX, uint32_t* __restrict__ pkeys,
-                             uint32_t* __restrict__ pvals) {
-  uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nv) return;
-  uint32_t i = dvals[s];
-  ushort4 r = rect[i];
-  uint32_t o = off[s];
-  for (int ty = r.y; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.z; ++tx) {
-      pkeys[o] = (uint32_t)(ty * TX + tx);
-      pvals[o] = i;
-      ++o;
+// Pair emission balanced over pairs: CTA c writes the pairs [1024 c,
+// 1024 c + 1024) in order.  Every visible Gaussian has at least one pair, so
+// the Gaussians (depth order) covering a chunk are at most 1024 consecutive
+// entries of the offsets; they are staged in shared memory and each pair finds
+// its Gaussian there by binary search, then its tile from its index inside
+// the Gaussian's tile rect (row-major).  Pairs at or beyond cap are not
+// written; they raise the camera's overflow flag (flag[0], sticky until the
+// host clears it, the pair count needed in flag[1]) and step_flag.
+constexpr int EP_THREADS = 256;
+constexpr int EP_CHUNK = 1024;
+
+__device__ __forceinline__ uint32_t last_le(const uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
+  // largest i < n with a[i] <= x (a non-decreasing, a[0] <= x)
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(EP_THREADS) k_emit_pairs(const uint32_t* __restrict__ nv_dev,
+                                                          const uint32_t* __restrict__ np_dev,
+                                                          const uint32_t* __restrict__ dvals,
+                                                          const ushort4* __restrict__ rect,
+                                                          const uint32_t* __restrict__ off, int TX,
+                                                          uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                                          uint64_t cap, uint32_t* flag, uint32_t* step_flag) {
+  __shared__ uint32_t s_off[EP_CHUNK];
+  __shared__ uint32_t s_id[EP_CHUNK];
+  __shared__ ushort4 s_rect[EP_CHUNK];
+  __shared__ uint32_t s_lo, s_cnt;
+  const uint32_t nv = *nv_dev;
+  const uint64_t np_all = *np_dev;
+  const uint32_t np = (uint32_t)(np_all < cap ? np_all : cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && np_all > cap) {
+    atomicOr(flag, 1u);
+    atomicMax(flag + 1, (uint32_t)(np_all > 0xFFFFFFFFull ? 0xFFFFFFFFull : np_all));
+    if (step_flag) atomicOr(step_flag, 1u);
+  }
+  for (uint32_t p0 = blockIdx.x * EP_CHUNK; p0 < np; p0 += gridDim.x * EP_CHUNK) {
+    const uint32_t p1 = min(p0 + EP_CHUNK, np) - 1;
+    if (threadIdx.x == 0) {
+      const uint32_t lo = last_le(off, nv, p0), hi = last_le(off, nv, p1);
+      s_lo = lo;
+      s_cnt = hi - lo + 1;
     }
+    __syncthreads();
+    const uint32_t lo = s_lo, cnt = s_cnt;
+    for (uint32_t e = threadIdx.x; e < cnt; e += EP_THREADS) {
+      const uint32_t id = dvals[lo + e];
+      s_off[e] = off[lo + e];
+      s_id[e] = id;
+      s_rect[e] = rect[id];
+    }
+    __syncthreads();
+    for (uint32_t p = p0 + threadIdx.x; p <= p1; p += EP_THREADS) {
+      const uint32_t k = last_le(s_off, cnt, p);
+      const ushort4 r = s_rect[k];
+      const uint32_t w = (uint32_t)(r.z - r.x);
+      const uint32_t loc = p - s_off[k];
+      const uint32_t dy = loc / w;
+      pkeys[p] = (uint32_t)((r.y + dy) * TX + r.x + (loc - dy * w));
+      pvals[p] = s_id[k];
+    }
+    __syncthreads();
+  }
 }
 
-__global__ void k_ranges(uint64_t np, const uint32_t* __restrict__ pkeys, uint2* __restrict__ ranges) {
-  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  uint32_t t = pkeys[p];
-  if (p == 0 || pkeys[p - 1] != t) ranges[t].x = (uint32_t)p;
-  if (p == np - 1 || pkeys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+// Tile order of the raster launches, longest pair list first (so the long
+// tiles do not start last): key 65535 - min(length, 65535), stable.
+__global__ void k_tile_keys(const uint2* __restrict__ ranges, uint32_t tiles, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals, uint32_t* __restrict__ n_out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *n_out = tiles;
+  if (t >= tiles) return;
+  const uint2 r = ranges[t];
+  const uint32_t len = r.y - r.x;
+  keys[t] = 0xFFFFu - (len < 0xFFFFu ? len : 0xFFFFu);
+  vals[t] = t;
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, const uint32_t* __restrict__ pkeys,
+                         uint2* __restrict__ ranges) {
+  uint64_t np = *np_dev;
+  if (np > cap) np = cap;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t t = pkeys[p];
+    if (p == 0 || pkeys[p - 1] != t) ranges[t].x = (uint32_t)p;
+    if (p == np - 1 || pkeys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+  }
 }
 
 // Raster CTA: one 16x16 tile, 128 threads in 4 warps; each warp owns an 8x8
@@ -335,12 +406,13 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
                                                          const float4* __restrict__ conic_o,
                                                          const float4* __restrict__ rgb, int W, int H, int TX,
                                                          float3 bg, float* __restrict__ img,
-                                                         float* __restrict__ t_final, int* __restrict__ n_last) {
+                                                         float* __restrict__ t_final, int* __restrict__ n_last,
+                                                         const uint32_t* __restrict__ order) {
   __shared__ float4 s_a[R_BATCH];  // x, y, A, B
   __shared__ float4 s_b[R_BATCH];  // C, opacity, r, g
   __shared__ float s_c[R_BATCH];   // b
   __shared__ float2 s_h[R_BATCH];  // alpha box half-sizes
-  const int tile = blockIdx.x;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const WarpPix q = warp_pixels(tile, TX);
   const uint2 r = ranges[tile];
   const int n = (int)(r.y - r.x);
@@ -431,14 +503,14 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
                                                          float3 bg, const float* __restrict__ t_final,
                                                          const int* __restrict__ n_last,
                                                          const float* __restrict__ dl_dimg, float* __restrict__ g2,
-                                                         uint64_t V) {
+                                                         uint64_t V, const uint32_t* __restrict__ order) {
   __shared__ uint32_t s_id[R_BATCH];
   __shared__ float4 s_a[R_BATCH];
   __shared__ float4 s_b[R_BATCH];
   __shared__ float s_c[R_BATCH];
   __shared__ float2 s_h[R_BATCH];
   __shared__ int s_max;
-  const int tile = blockIdx.x;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const WarpPix q = warp_pixels(tile, TX);
   const uint2 r = ranges[tile];
   const float fpx = (float)q.px;
@@ -714,7 +786,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
                                                               const float4* __restrict__ conic_o,
                                                               const float* __restrict__ g2, uint64_t V,
                                                               float* __restrict__ grad, uint64_t Vg, int mode,
-                                                              unsigned cpi) {
+                                                              unsigned cpi, const uint8_t* __restrict__ touched) {
   const unsigned item = blockIdx.x / cpi;
   const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
   const uint32_t B = rl.B;
@@ -722,7 +794,9 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   const uint64_t i = (uint64_t)item * B + lane;
   if (lane >= rl.item_count[item]) return;
   const bool vis = ntiles[i] != 0;
-  if (!vis && mode != 0) return;
+  // mode 0 stores the rows the optimiser reads (touched by the batch; all if
+  // touched is null), zero where this camera does not see the Gaussian
+  if (!vis && (mode != 0 || (touched && !touched[i]))) return;
   const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
   const float* p = rl.base + sbase;
   const __nv_bfloat16* q16 = sh16(rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride, B, lane);
@@ -746,70 +820,95 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   }
 }
 
+// Masked Adam over the render list.  CTA (item chunk, field group): each
+// thread updates ADAM_FG consecutive fields of one Gaussian, so a warp keeps
+// several independent coalesced loads of p, g, m and v in flight.  The bias
+// corrections 1 / (1 - beta^step) of the item's block come precomputed.
+constexpr int ADAM_FG = 8;
+constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
+
 template <bool BF>
 __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
                                                     const uint8_t* __restrict__ touched,
+                                                    const float2* __restrict__ bias,
                                                     const uint32_t* __restrict__ block_step, uint64_t V, float lr,
-                                                    float b1, float b2, float eps, unsigned cpi) {
+                                                    float b1, float b2, float eps, unsigned cpi,
+                                                    const uint32_t* __restrict__ abort_flag) {
+  if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
   const unsigned item = blockIdx.x / cpi;
   const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
   const uint32_t B = rl.B;
   if (lane >= B) return;
   const uint64_t i = (uint64_t)item * B + lane;
   if (lane >= rl.item_count[item] || !touched[i]) return;
-  const uint32_t blk = rl.item_block[item];
-  const uint32_t step = block_step[blk];
-  const float tau = (float)step;
-  const float c1 = 1.f - powf(b1, tau), c2 = 1.f - powf(b2, tau);
-  const float ic1 = 1.f / c1, ic2 = 1.f / c2;
+  const float2 bc = bias[item];
+  const float ic1 = bc.x, ic2 = bc.y;
+  const int f0 = blockIdx.y * ADAM_FG;
   float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
   float* p = slot + lane;
   if (!BF) {
     float* m = p + rl.m_off;
     float* v = p + rl.v_off;
-#pragma unroll 4
-    for (int f = 0; f < D; ++f) {
-      const uint64_t o = (uint64_t)f * B;
-      float gf = grad[(uint64_t)f * V + i];
-      float mf = b1 * m[o] + (1.f - b1) * gf;
-      float vf = b2 * v[o] + (1.f - b2) * gf * gf;
-      m[o] = mf;
-      v[o] = vf;
-      p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        float gf = grad[(uint64_t)f * V + i];
+        float mf = b1 * m[o] + (1.f - b1) * gf;
+        float vf = b2 * v[o] + (1.f - b2) * gf * gf;
+        m[o] = mf;
+        v[o] = vf;
+        p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+      }
     }
   } else {
-    __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
+    __nv_bfloat16* q16 = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
     __nv_bfloat16* m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
     __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
     const bool sr = rl.sr != 0;
+    const uint32_t blk = rl.item_block[item];
+    const uint32_t step = block_step[blk];
     const uint64_t gid = (uint64_t)blk * B + lane;
     const uint64_t key0 = ((uint64_t)rl.seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20);
-#pragma unroll 4
-    for (int f = 0; f < D; ++f) {
-      const uint64_t o = (uint64_t)f * B;
-      float gf = grad[(uint64_t)f * V + i];
-      float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
-      float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
-      const float upd = lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
-      const uint64_t key = key0 + (uint64_t)f * 4;
-      m[o] = to_bf16(mf, sr, key);
-      v[o] = to_bf16(vf, sr, key + 1);
-      if (f < F_BF16) {
-        p[o] -= upd;
-      } else {
-        const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
-        q[o16] = to_bf16(__bfloat162float(q[o16]) - upd, sr, key + 2);
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        float gf = grad[(uint64_t)f * V + i];
+        float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
+        float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
+        const float upd = lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+        const uint64_t key = key0 + (uint64_t)f * 4;
+        m[o] = to_bf16(mf, sr, key);
+        v[o] = to_bf16(vf, sr, key + 1);
+        if (f < F_BF16) {
+          p[o] -= upd;
+        } else {
+          const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
+          q16[o16] = to_bf16(__bfloat162float(q16[o16]) - upd, sr, key + 2);
+        }
       }
     }
   }
 }
 
 __global__ void k_mark_touched(RenderList rl, const uint32_t* __restrict__ item_touched, uint32_t* block_step,
-                               uint8_t* dirty) {
+                               uint8_t* dirty, uint32_t* abort_flag, float b1, float b2, float2* __restrict__ bias) {
   unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (abort_flag && abort_flag[0]) {
+    if (j == 0) abort_flag[1] += 1;  // steps dropped since the overflow
+    return;
+  }
   if (j >= rl.n_items || !item_touched[j]) return;
-  block_step[rl.item_block[j]] += 1;
+  const uint32_t st = block_step[rl.item_block[j]] + 1;
+  block_step[rl.item_block[j]] = st;
   if (dirty) dirty[rl.item_slot[j]] = 1;
+  if (bias) {
+    const float tau = (float)st;
+    bias[j] = make_float2(1.f / (1.f - powf(b1, tau)), 1.f / (1.f - powf(b2, tau)));
+  }
 }
 
 __device__ __forceinline__ float block_reduce(float v, float* sm, bool is_max, bool is_min) {
@@ -828,10 +927,10 @@ __device__ __forceinline__ float block_reduce(float v, float* sm, bool is_max, b
 }
 
 __global__ void __launch_bounds__(256) k_bounds(RenderList rl, const uint32_t* __restrict__ only,
-                                               float4* __restrict__ spheres) {
+                                               float4* __restrict__ spheres, const uint32_t* __restrict__ abort_flag) {
   __shared__ float sm[8];
   const unsigned item = blockIdx.x;
-  if (only && !only[item]) return;
+  if ((only && !only[item]) || (abort_flag && *abort_flag)) return;
   const uint32_t B = rl.B, cnt = rl.item_count[item];
   const float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -958,6 +1057,12 @@ DevCam make_devcam(const tgs_camera& c) {
   return d;
 }
 
+static int bits_for(uint64_t n) {
+  int b = 1;
+  while ((1ull << b) < n) ++b;
+  return b;
+}
+
 void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h) {
   cs.cap_v = cap_v;
   cs.cap_pix = (uint64_t)max_w * max_h;
@@ -977,8 +1082,12 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.ranges, cs.cap_tiles * sizeof(uint2)));
   TGS_CUDA(cudaMalloc(&cs.t_final, cs.cap_pix * sizeof(float)));
   TGS_CUDA(cudaMalloc(&cs.n_last, cs.cap_pix * sizeof(int)));
-  TGS_CUDA(cudaMalloc(&cs.counters, 4 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.counters, 8 * sizeof(uint32_t)));
   TGS_CUDA(cudaMallocHost(&cs.counters_host, 4 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.tkeys, 2 * cs.cap_tiles * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.torder, 2 * cs.cap_tiles * sizeof(uint32_t)));
+  TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_counts, cudaEventDisableTiming));
+  TGS_CUDA(cudaMemset(cs.counters, 0, 8 * sizeof(uint32_t)));
   cs.cap_pairs = 0;
   cam_state_grow_pairs(cs, cap_pairs > 0 ? cap_pairs : 1024, 0);
 }
@@ -999,6 +1108,7 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
   size_t sb = radix_scratch_bytes(want);
   size_t sc = scan_scratch_bytes(want);
   if (sc > sb) sb = sc;
+  if (radix_dev_scratch_bytes(want) > sb) sb = radix_dev_scratch_bytes(want);
   if (sb > cs.scratch_bytes) {
     if (s) TGS_CUDA(cudaStreamSynchronize(s));
     if (cs.scratch) TGS_CUDA(cudaFree(cs.scratch));
@@ -1009,18 +1119,15 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
 
 void cam_state_free(CamState& cs) {
   void* ptrs[] = {cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.dkeys,
-                  cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch};
+                  cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch,
+                  cs.tkeys, cs.torder};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (cs.counters_host) cudaFreeHost(cs.counters_host);
+  if (cs.ev_counts) cudaEventDestroy(cs.ev_counts);
   cs = CamState();
 }
 
-static int bits_for(uint64_t n) {
-  int b = 1;
-  while ((1ull << b) < n) ++b;
-  return b;
-}
 
 void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
                     uint8_t* touched, uint32_t* item_touched, cudaStream_t s, StageTimer* tm) {
@@ -1031,11 +1138,14 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   TGS_CHECK((uint64_t)cam.W * cam.H <= cs.cap_pix && (uint64_t)cam.TX * cam.TY <= cs.cap_tiles, TGS_ERR_CAPACITY,
             "image larger than the configured maximum");
   cs.W = cam.W; cs.H = cam.H; cs.TX = cam.TX; cs.TY = cam.TY;
+  cam_state_counts(cs, false);  // harvest an earlier render's counts if they arrived (grid hints)
+  cs.counts_valid = false;
   const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
-  cs.n_vis = 0;
-  cs.n_pairs = 0;
+  uint32_t* nv_dev = cs.counters;      // visible Gaussians
+  uint32_t* np_dev = cs.counters + 1;  // pairs (before the capacity clamp)
   TGS_CUDA(cudaMemsetAsync(cs.ranges, 0, tiles * sizeof(uint2), s));
+  TGS_CUDA(cudaMemsetAsync(cs.counters, 0, 2 * sizeof(uint32_t), s));  // the overflow words stay
   if (V > 0) {
     unsigned cpi = div_up(rl.B, PP_THREADS);
     PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
@@ -1047,39 +1157,63 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
     TGS_LAUNCHED();
     tm->end(StageTimer::PRE, s);
     tm->begin(StageTimer::SORT, s);
-    exclusive_scan_u32(cs.scan, cs.scan, cs.counters, V, cs.scratch, s);
+    // the sizes stay on the device: no host round trip inside a render
+    exclusive_scan_u32(cs.scan, cs.scan, nv_dev, V, cs.scratch, s);
     k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
     TGS_LAUNCHED();
-    TGS_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    TGS_CUDA(cudaStreamSynchronize(s));
-    cs.n_vis = cs.counters_host[0];
-  }
-  const uint64_t nv = cs.n_vis;
-  if (nv > 0) {
-    radix_sort_pairs(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv, 32, cs.scratch, s);
-    k_gather_counts<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.ntiles, cs.scan);
+    // the counts of an earlier render size the sorts' grids
+    radix_sort_pairs_dev(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv_dev, V, 32, cs.scratch, s,
+                         cs.hint_nv);
+    k_gather_counts<<<div_up(V, 256), 256, 0, s>>>(nv_dev, cs.dvals, cs.ntiles, cs.scan);
     TGS_LAUNCHED();
-    exclusive_scan_u32(cs.scan, cs.scan, cs.counters + 1, nv, cs.scratch, s);
-    TGS_CUDA(cudaMemcpyAsync(cs.counters_host + 1, cs.counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    TGS_CUDA(cudaStreamSynchronize(s));
-    cs.n_pairs = cs.counters_host[1];
-    cam_state_grow_pairs(cs, cs.n_pairs, s);
-    const uint64_t np = cs.n_pairs;
-    if (np > 0) {
-      k_emit_pairs<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys, cs.pvals);
-      TGS_LAUNCHED();
-      radix_sort_pairs(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np,
-                       bits_for(tiles), cs.scratch, s);
-      k_ranges<<<div_up(np, 256), 256, 0, s>>>(np, cs.pkeys, cs.ranges);
-      TGS_LAUNCHED();
-    }
+    exclusive_scan_u32_dev(cs.scan, cs.scan, np_dev, nv_dev, V, cs.scratch, s);
+    k_emit_pairs<<<4 * NSM, EP_THREADS, 0, s>>>(nv_dev, np_dev, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys,
+                                                cs.pvals, cs.cap_pairs, cs.counters + 2, cs.step_flag);
+    TGS_LAUNCHED();
+    radix_sort_pairs_dev(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np_dev, cs.cap_pairs,
+                         bits_for(tiles), cs.scratch, s, cs.hint_np);
+    k_ranges<<<2 * NSM, 256, 0, s>>>(np_dev, cs.cap_pairs, cs.pkeys, cs.ranges);
+    TGS_LAUNCHED();
+    k_tile_keys<<<div_up(tiles, 256), 256, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.tkeys, cs.torder, cs.counters + 4);
+    TGS_LAUNCHED();
+    radix_sort_pairs_dev(cs.tkeys, cs.torder, cs.tkeys + cs.cap_tiles, cs.torder + cs.cap_tiles, cs.counters + 4,
+                         tiles, 16, cs.scratch, s);
+    cs.order_valid = true;
+    tm->end(StageTimer::SORT, s);
+  } else {
+    cs.order_valid = false;
   }
-  tm->end(StageTimer::SORT, s);
   tm->begin(StageTimer::FWD, s);
   k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, image, cs.t_final, cs.n_last);
+                                                   cam.TX, bg3, image, cs.t_final, cs.n_last,
+                                                   cs.order_valid ? cs.torder : nullptr);
   TGS_LAUNCHED();
   tm->end(StageTimer::FWD, s);
+  // the counts reach the host asynchronously (read by cam_state_counts)
+  TGS_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TGS_CUDA(cudaEventRecord(cs.ev_counts, s));
+  cs.counts_pending = true;
+}
+
+bool cam_state_counts(CamState& cs, bool wait) {
+  if (cs.counts_pending) {
+    if (wait) {
+      TGS_CUDA(cudaEventSynchronize(cs.ev_counts));
+    } else {
+      cudaError_t e = cudaEventQuery(cs.ev_counts);
+      if (e == cudaErrorNotReady) return false;
+      TGS_CUDA(e);
+    }
+    cs.n_vis = cs.counters_host[0];
+    cs.n_pairs = cs.counters_host[1];
+    cs.overflow = cs.counters_host[2] != 0;
+    cs.pairs_needed = cs.counters_host[3];
+    cs.hint_nv = cs.n_vis;
+    cs.hint_np = cs.n_pairs < cs.cap_pairs ? cs.n_pairs : cs.cap_pairs;
+    cs.counts_pending = false;
+    cs.counts_valid = true;
+  }
+  return cs.counts_valid;
 }
 
 // The forward of render_forward on caller-provided fixed buffers: nothing is
@@ -1098,6 +1232,7 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
   cs.n_pairs = 0;
   uint32_t cnt = 0;
   TGS_CUDA(cudaMemsetAsync(cs.ranges, 0, tiles * sizeof(uint2), s));
+  TGS_CUDA(cudaMemsetAsync(cs.counters, 0, 4 * sizeof(uint32_t), s));
   if (V > 0) {
     unsigned cpi = div_up(rl.B, PP_THREADS);
     PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
@@ -1113,7 +1248,7 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
   const uint64_t nv = cs.n_vis;
   if (nv > 0) {
     radix_sort_pairs(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv, 32, cs.scratch, s);
-    k_gather_counts<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.ntiles, cs.scan);
+    k_gather_counts<<<div_up(nv, 256), 256, 0, s>>>(cs.counters, cs.dvals, cs.ntiles, cs.scan);
     TGS_LAUNCHED();
     exclusive_scan_u32(cs.scan, cs.scan, cs.counters + 1, nv, cs.scratch, s);
     TGS_CUDA(cudaMemcpyAsync(&cnt, cs.counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -1122,16 +1257,18 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
     TGS_CHECK(cs.n_pairs <= cs.cap_pairs, TGS_ERR_CAPACITY, "tile/Gaussian pairs exceed the fixed maximum");
     const uint64_t np = cs.n_pairs;
     if (np > 0) {
-      k_emit_pairs<<<div_up(nv, 256), 256, 0, s>>>(nv, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys, cs.pvals);
+      k_emit_pairs<<<4 * NSM, EP_THREADS, 0, s>>>(cs.counters, cs.counters + 1, cs.dvals, cs.rect, cs.scan, cam.TX,
+                                                  cs.pkeys, cs.pvals, cs.cap_pairs, cs.counters + 2, nullptr);
       TGS_LAUNCHED();
       radix_sort_pairs(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np,
                        bits_for(tiles), cs.scratch, s);
-      k_ranges<<<div_up(np, 256), 256, 0, s>>>(np, cs.pkeys, cs.ranges);
+      k_ranges<<<div_up(np, 256), 256, 0, s>>>(cs.counters + 1, cs.cap_pairs, cs.pkeys, cs.ranges);
       TGS_LAUNCHED();
     }
   }
   k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, image, cs.t_final, cs.n_last);
+                                                   cam.TX, bg3, image, cs.t_final, cs.n_last, nullptr);
+  cs.order_valid = false;
   TGS_LAUNCHED();
 }
 
@@ -1141,49 +1278,53 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
   const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
   if (V == 0) return;
   TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * cs.cap_v * sizeof(float), s));
-  if (cs.n_pairs == 0) return;
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
   k_raster_bwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.cap_v);
+                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.cap_v,
+                                                   cs.order_valid ? cs.torder : nullptr);
   TGS_LAUNCHED();
 }
 
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
-                            cudaStream_t s) {
-  if (rl.capacity() == 0 || (cs.n_vis == 0 && mode != 0)) return;
-  unsigned cpi = div_up(rl.B, PP_THREADS);
-  if (rl.bf16)
-    k_preprocess_bwd<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi);
-  else
-    k_preprocess_bwd<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi);
-  TGS_LAUNCHED();
-}
-
-void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const uint32_t* block_step,
-                      float lr, float b1, float b2, float eps, cudaStream_t s) {
+                            cudaStream_t s, const uint8_t* touched) {
   if (rl.capacity() == 0) return;
   unsigned cpi = div_up(rl.B, PP_THREADS);
   if (rl.bf16)
-    k_adam<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2, eps,
-                                                        cpi);
+    k_preprocess_bwd<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
+                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi, touched);
   else
-    k_adam<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, grad, touched, block_step, rl.capacity(), lr, b1, b2,
-                                                         eps, cpi);
+    k_preprocess_bwd<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
+                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi, touched);
+  TGS_LAUNCHED();
+}
+
+void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const float2* bias,
+                      const uint32_t* block_step, float lr, float b1, float b2, float eps, cudaStream_t s,
+                      const uint32_t* abort_flag) {
+  if (rl.capacity() == 0) return;
+  unsigned cpi = div_up(rl.B, PP_THREADS);
+  const dim3 grid(rl.n_items * cpi, ADAM_GROUPS);
+  if (rl.bf16)
+    k_adam<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, touched, bias, block_step, rl.capacity(), lr, b1, b2, eps, cpi,
+                                            abort_flag);
+  else
+    k_adam<false><<<grid, PP_THREADS, 0, s>>>(rl, grad, touched, bias, block_step, rl.capacity(), lr, b1, b2, eps, cpi,
+                                             abort_flag);
   TGS_LAUNCHED();
 }
 
 void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
-                         cudaStream_t s) {
+                         cudaStream_t s, uint32_t* abort_flag, float b1, float b2, float2* bias) {
   if (rl.n_items == 0) return;
-  k_mark_touched<<<div_up(rl.n_items, 256), 256, 0, s>>>(rl, item_touched, block_step, dirty);
+  k_mark_touched<<<div_up(rl.n_items, 256), 256, 0, s>>>(rl, item_touched, block_step, dirty, abort_flag, b1, b2,
+                                                         bias);
   TGS_LAUNCHED();
 }
 
-void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s) {
+void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s,
+                  const uint32_t* abort_flag) {
   if (rl.n_items == 0) return;
-  k_bounds<<<rl.n_items, 256, 0, s>>>(rl, only_flag, spheres);
+  k_bounds<<<rl.n_items, 256, 0, s>>>(rl, only_flag, spheres, abort_flag);
   TGS_LAUNCHED();
 }
 

@@ -54,27 +54,39 @@ struct CamState {
   uint32_t* pvals = nullptr;
   // per tile / pixel
   uint2* ranges = nullptr;
+  uint32_t* tkeys = nullptr;   // 2 x cap_tiles: tile-order sort keys (ping-pong)
+  uint32_t* torder = nullptr;  // 2 x cap_tiles: tiles, longest pair list first
+  bool order_valid = false;
   float* t_final = nullptr;
   int* n_last = nullptr;
   // scratch for scans and sorts
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  uint32_t* counters = nullptr;  // device [4]: n_vis, n_pairs
-  uint32_t* counters_host = nullptr;  // pinned mirror
-  // results of the last render
-  uint64_t n_vis = 0, n_pairs = 0;
+  uint32_t* counters = nullptr;  // device [8]: n_vis, n_pairs (before the clamp), overflow, pairs needed, tiles
+  uint32_t* counters_host = nullptr;  // pinned mirror, copied at the end of each render
+  cudaEvent_t ev_counts = nullptr;    // recorded after that copy
+  uint32_t* step_flag = nullptr;      // optional device word raised with the overflow flag
+  // results of the last render (valid after cam_state_counts)
+  uint64_t n_vis = 0, n_pairs = 0, pairs_needed = 0;
+  uint64_t hint_nv = 0, hint_np = 0;  // counts of the latest harvested render (grid sizes)
+  bool overflow = false, counts_pending = false, counts_valid = false;
   int W = 0, H = 0, TX = 0, TY = 0;
 };
 
 void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h);
 void cam_state_free(CamState& cs);
 void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
+// Reads the last render's counts into n_vis / n_pairs / overflow; wait =
+// false returns false if they have not reached the host yet.
+bool cam_state_counts(CamState& cs, bool wait);
 
 // Forward: preprocess -> visible compaction -> depth sort -> pair emission ->
 // tile sort -> ranges -> compositing.  touched (render-list bytes, may be
 // null) gets 1 for visible Gaussians; item_touched (per item, may be null)
-// gets 1 for items with a visible Gaussian.  Synchronises the stream twice
-// to read the visible and pair counts.
+// gets 1 for items with a visible Gaussian.  No host synchronisation: the
+// visible and pair counts stay on the device, pairs beyond cs.cap_pairs are
+// dropped and flag an overflow (counters[2], and *cs.step_flag if set); the
+// counts reach the host asynchronously.
 void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], CamState& cs, float* image,
                     uint8_t* touched, uint32_t* item_touched, cudaStream_t s, StageTimer* tm = nullptr);
 
@@ -91,19 +103,28 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
 // position's gradient (zero when invisible) into a local [59][rl.capacity()] array,
 // mode 1 adds visible gradients to it, mode 2 adds into a pool with the
 // render list's slot layout (grad = pool base).
+// touched (render-list bytes, may be null): mode 0 then skips the rows no
+// camera of the batch touched (the optimiser does not read them).
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
-                            cudaStream_t s);
+                            cudaStream_t s, const uint8_t* touched = nullptr);
 
 // Masked Adam over the render list: rows with touched != 0 update params and
 // moments in the pool; `grad` is the local [59][rl.capacity()] array; step counters per
-// block id (already incremented for this step).
-void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const uint32_t* block_step,
-                      float lr, float b1, float b2, float eps, cudaStream_t s);
+// block id (already incremented for this step).  Nothing is updated while
+// *abort_flag (device, may be null) is set.
+// bias: per item (1 / (1 - b1^step), 1 / (1 - b2^step)) from mark_touched_blocks.
+void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const float2* bias,
+                      const uint32_t* block_step, float lr, float b1, float b2, float eps, cudaStream_t s,
+                      const uint32_t* abort_flag = nullptr);
 
 // Per-item bookkeeping before Adam: for items with item_touched != 0,
-// block_step[block] += 1 and dirty[slot] = 1.
+// block_step[block] += 1 and dirty[slot] = 1.  While abort_flag[0] is set
+// (device, may be null) nothing is marked and abort_flag[1] counts the step.
+// bias (per item, may be null) receives the Adam bias corrections of the
+// incremented step.
 void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
-                         cudaStream_t s);
+                         cudaStream_t s, uint32_t* abort_flag = nullptr, float b1 = 0.9f, float b2 = 0.999f,
+                         float2* bias = nullptr);
 
 // touched[j * B + l] |= (Gaussian l of item j had a non-empty tile rect in cs).
 void mark_visible_bytes(const RenderList& rl, const CamState& cs, uint8_t* touched, cudaStream_t s);
@@ -117,7 +138,8 @@ void adam_dense(float* params, const float* grad, float* m1, float* m2, const ui
 // Bounding spheres (Sec. 3.3 "Level 1") of the listed blocks: centre = middle
 // of the means' box, radius = max(|mu - c| + 3 max exp(log-scale)); written to
 // spheres[block].  only_flag (per item, may be null) restricts to flagged items.
-void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s);
+void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s,
+                  const uint32_t* abort_flag = nullptr);
 
 // Photometric loss over n values: writes dL/dimage and accumulates the sum of
 // per-value losses into *loss_sum (device float, zeroed by the caller).

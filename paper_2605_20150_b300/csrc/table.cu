@@ -18,6 +18,20 @@
 
 namespace tgs {
 
+// Distance between the centres (-R^T t) of two cameras.
+static double camera_distance(const tgs_camera& a, const tgs_camera& b) {
+  double d2 = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double ca = 0.0, cb = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      ca -= (double)a.world_to_cam[4 * j + i] * a.world_to_cam[4 * j + 3];
+      cb -= (double)b.world_to_cam[4 * j + i] * b.world_to_cam[4 * j + 3];
+    }
+    d2 += (ca - cb) * (ca - cb);
+  }
+  return std::sqrt(d2);
+}
+
 namespace {
 
 template <class T>
@@ -148,12 +162,22 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaMallocHost(&rl_host, 3ull * max_items * sizeof(uint32_t)));
   const uint64_t pix = (uint64_t)cfg.max_width * cfg.max_height;
   cams.resize(cfg.max_batch);
-  for (auto& cs : cams) cam_state_alloc(cs, V_cap, 4 * V_cap, (int)cfg.max_width, (int)cfg.max_height);
+  dalloc(abort_dev, 2);
+  TGS_CUDA(cudaMallocHost(&abort_host, 2 * sizeof(uint32_t)));
+  for (auto& cs : cams) {
+    // default pair capacity: two pairs per render-list Gaussian or 16 per
+    // pixel (a mean tile list of 4,096 splats), whichever is larger
+    const uint64_t def_pairs = std::max<uint64_t>(2 * V_cap, 16 * pix);
+    cam_state_alloc(cs, V_cap, cfg.pair_capacity ? cfg.pair_capacity : def_pairs, (int)cfg.max_width,
+                    (int)cfg.max_height);
+    cs.step_flag = abort_dev;
+  }
   dalloc(images, cfg.max_batch * pix * 3);
   dalloc(dl_dimg, cfg.max_batch * pix * 3);
   dalloc(targets_buf, cfg.max_batch * pix * 3);
   dalloc(touched, V_cap);
   dalloc(item_touched, max_items);
+  dalloc(item_bias, max_items);
   dalloc(grad_local, (uint64_t)D * V_cap);
   dalloc(loss_dev, 4);
   TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
@@ -253,10 +277,10 @@ void Table::destroy() {
   for (auto& cs : cams) cam_state_free(cs);
   void* dev[] = {pool, spheres, spheres_snap, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
                  kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
-                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, grad_local,
-                 loss_dev};
+                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, item_bias, grad_local,
+                 loss_dev, abort_dev};
   for (void* p : dev) dfree(p);
-  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned};
+  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host};
   for (void* p : hst)
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
@@ -311,9 +335,15 @@ void Table::prepare_enqueue_predicted(Prepared& out) {
     int idx = (int)hist.size() - MLP_HIST + s;
     h[s] = hist[idx < 0 ? 0 : idx];
   }
+  // reach: twice the longest camera move of the history per predicted step
+  int hmax = 0;
+  for (int q = 0; q < MLP_OUT; ++q)
+    if (pred_mask >> q & 1u) hmax = q + 1;
+  double vmax = 0.0;
+  for (int s = 1; s < MLP_HIST; ++s) vmax = std::max(vmax, camera_distance(h[s - 1], h[s]));
+  const float reach = (float)(2.0 * hmax * vmax);
   TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
-  mlp_forward(*predictor, spheres, K, h, nullptr, false, ctl);
-  mlp_threshold(predictor->z3, K, pred_mask, pred_threshold, kvis, ctl);
+  mlp_predict_near(*predictor, spheres, K, h, reach, pred_mask, pred_threshold, kvis, ctl);
   TGS_CUDA(cudaMemcpyAsync(kvis_union, kvis, words * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctl));
   select_enqueue(1, out, false);
 }
@@ -557,8 +587,6 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     DevCam dc = make_devcam(p.cams[j]);
     float* img = image_out && J == 1 ? image_out : images + (uint64_t)j * pix * 3;
     render_forward(rl, dc, cfg.bg, cams[j], img, touched, item_touched, comp, &timer);
-    stats.last_pairs = cams[j].n_pairs;
-    stats.last_visible = cams[j].n_vis;
   }
   stats.last_render_blocks = n_items;
   if (backward) {
@@ -582,17 +610,18 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
       render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
       timer.end(StageTimer::BWD, comp);
       timer.begin(StageTimer::PBWD, comp);
-      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp);
+      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp, touched);
       timer.end(StageTimer::PBWD, comp);
     }
     timer.begin(StageTimer::ADAM, comp);
-    mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp);
-    adam_render_list(rl, grad_local, touched, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp);
+    mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias);
+    adam_render_list(rl, grad_local, touched, item_bias, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp,
+                     abort_dev);
     timer.end(StageTimer::ADAM, comp);
     // the next batch's cull (control stream) reads the bounds first
     TGS_CUDA(cudaStreamWaitEvent(comp, ev_ctl, 0));
     timer.begin(StageTimer::BOUNDS, comp);
-    block_bounds(rl, item_touched, spheres, comp);
+    block_bounds(rl, item_touched, spheres, comp, abort_dev);
     timer.end(StageTimer::BOUNDS, comp);
     for (uint32_t j = 0; j < n_items; ++j) dirty_host[p.render_slots[j]] = 1;
     stats.steps++;
@@ -616,6 +645,7 @@ static bool same_cams(const std::vector<tgs_camera>& a, const tgs_camera* b, uin
 void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint32_t nJ, const float* targets_dev,
                  const float* targets_host, cudaStream_t user, float* loss_out) {
   TGS_CHECK(cs && J >= 1, TGS_ERR_INVALID, "tgs_step: no cameras");
+  check_overflow(false);
   if (!(prep.valid && same_cams(prep.cams, cs, J))) {
     // reactive path: select and stream this batch's working set now
     Prepared p;
@@ -648,6 +678,7 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   if (loss_out) {
     TGS_CUDA(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, comp));
     TGS_CUDA(cudaStreamSynchronize(comp));
+    check_overflow(true);
     const uint32_t Jc = (uint32_t)cur.cams.size();
     *loss_out = loss_host[0] / (float)((uint64_t)Jc * cur.cams[0].width * cur.cams[0].height * 3);
   }
@@ -661,7 +692,32 @@ void Table::render(const tgs_camera& cam, float* image_dev, cudaStream_t user) {
   issue_early(p);
   issue_evictions_and_late(p);
   compute(p, nullptr, nullptr, user, false, image_dev);
+  // a render returns a complete image: after an overflow the buffers grow and
+  // the same selection is rendered again
+  if (check_overflow(true)) compute(p, nullptr, nullptr, user, false, image_dev);
   prep = Prepared();
+}
+
+bool Table::check_overflow(bool wait) {
+  bool any = false;
+  uint64_t need = 0;
+  for (auto& cs : cams) {
+    if (!cam_state_counts(cs, wait) || !cs.overflow) continue;
+    any = true;
+    if (cs.pairs_needed > need) need = cs.pairs_needed;
+  }
+  if (!any) return false;
+  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  TGS_CUDA(cudaMemcpy(abort_host, abort_dev, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  stats.dropped_steps += abort_host[1];
+  stats.pair_overflows += 1;
+  for (auto& cs : cams) {
+    cam_state_grow_pairs(cs, need, comp);
+    TGS_CUDA(cudaMemset(cs.counters + 2, 0, 2 * sizeof(uint32_t)));
+    cs.overflow = false;
+  }
+  TGS_CUDA(cudaMemset(abort_dev, 0, 2 * sizeof(uint32_t)));
+  return true;
 }
 
 // Consistency barrier: every dirty resident block goes back to the host tier.

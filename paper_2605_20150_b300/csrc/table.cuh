@@ -70,6 +70,9 @@ struct Table {
   float* grad_local = nullptr;
   float* loss_dev = nullptr;
   float* loss_host = nullptr;
+  float2* item_bias = nullptr;     // per render-list item: Adam bias corrections of this step
+  uint32_t* abort_dev = nullptr;   // [2]: a render of a step overflowed its pairs; steps dropped since
+  uint32_t* abort_host = nullptr;  // pinned
 
   // host mirrors
   std::vector<int64_t> slot_of;          // K
@@ -123,6 +126,10 @@ struct Table {
   void render(const tgs_camera& cam, float* image_dev, cudaStream_t user);
   void flush();
   void collect_stall();
+  // Handles a pair-capacity overflow seen by a render (wait: block until the
+  // last renders' counts are on the host): grows the pair buffers, counts
+  // the dropped steps and clears the flag.  Returns true if one was handled.
+  bool check_overflow(bool wait);
   RenderList render_list(uint32_t n_items) const;
 };
 

@@ -168,3 +168,52 @@ def test_block_delta_two_cameras(orc, tgs):
         kacc = (out["r_next"] & vis.reshape(-1)).astype(np.uint8)
         r, age = out["r_next"], out["age"]
     table.close()
+
+
+def test_pair_overflow_skips_the_update_and_recovers(orc, tgs):
+    """A pair capacity far below the render's pairs: the step's update is
+    skipped (parameters and step counters unchanged), the capacity grows once
+    the host reads the count, and the next step matches the oracle."""
+    c, perm, Pm, tp = c1_inputs(orc)
+    camd = c["cams"][0]
+    cam = scenes.camera_array(camd)
+    _, Pt = orc.create(tp, 1250)
+    target = orc.render(Pt.astype(np.float64), cam)["img"].astype(np.float32)
+    table = tgs.TideTable(c["params"], block_size=1250, max_batch=1, max_width=256, max_height=256, loss=1,
+                          pair_capacity=100)
+    table.step([camd], target[None])
+    st = table.stats()
+    assert st["pair_overflows"] == 1 and st["dropped_steps"] == 1
+    p_g, m1, m2, steps = table.state()
+    assert np.array_equal(p_g, Pm) and not m1.any() and not steps.any()
+    lval = table.step([camd], target[None])
+    st = table.stats()
+    assert st["pair_overflows"] == 1 and st["dropped_steps"] == 1 and st["last_pairs"] > 1149
+    K = 16
+    sph = orc.block_spheres(Pm.astype(np.float64), 1250)
+    _, vis = orc.visible_blocks(sph, [cam])
+    P = Pm.astype(np.float64).copy()
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    o = orc.train_step(P, M1, M2, np.zeros(K, np.int64), 1250, np.nonzero(vis)[0], [cam], target[None], lr=1e-3,
+                       loss_kind=1)
+    assert abs(lval - o["loss"]) <= 1e-4 * o["loss"]
+    p_g, m1, m2, steps = table.state()
+    t = o["touched"].astype(bool)
+    assert rel_l2(m1[o["ids"]][t] / 0.1, o["grad"][t]) < 1e-3
+    table.close()
+
+
+def test_render_after_pair_overflow_is_complete(orc, tgs):
+    import torch
+    c, perm, Pm, tp = c1_inputs(orc)
+    camd = c["cams"][1]
+    table = tgs.TideTable(c["params"], block_size=1250, max_batch=1, max_width=256, max_height=256,
+                          pair_capacity=100)
+    img = torch.zeros(256, 256, 3, device="cuda")
+    table.render(camd, img)
+    st = table.stats()
+    assert st["pair_overflows"] == 1 and st["dropped_steps"] == 0
+    orec = orc.render(Pm.astype(np.float64), scenes.camera_array(camd))
+    err, frac = image_within(img.cpu().numpy(), orec)
+    assert err <= 1e-4 and frac < 0.05
+    table.close()
