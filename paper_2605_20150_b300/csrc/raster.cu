@@ -358,15 +358,18 @@ __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, cons
 }
 
 // Raster CTA: one 16x16 tile, 128 threads in 4 warps; each warp owns an 8x8
-// pixel square and each thread two vertically adjacent pixels of it.  Splats
-// are staged R_BATCH at a time in shared memory together with the half-sizes
-// of the box outside which their alpha is certainly below 1/255; a warp whose
-// square misses that box skips the splat (a warp-uniform branch, so results
-// are unchanged), otherwise each thread evaluates its pixels with predicated,
-// branch-free updates.
+// pixel square and each thread two vertically adjacent pixels of it.  The
+// warps are independent: each walks the tile's list 32 splats at a time,
+// lane l staging splat l of the batch in the warp's slice of shared memory
+// together with the test of its alpha box (outside which alpha < 1/255)
+// against the warp's square; a ballot of that test is the warp's work list,
+// taken in list order, so results are those of visiting every splat.  Pixels
+// are evaluated with predicated, branch-free updates; a warp stops when its
+// pixels are saturated (forward) and starts at the largest n_last of its
+// pixels (backward), without waiting for the other warps.
 constexpr int R_PPT = 2;
 constexpr int R_THREADS = TILE_PIX / R_PPT;  // 128
-constexpr int R_BATCH = 128;
+constexpr int R_WARPS = R_THREADS / 32;
 
 struct WarpPix {
   int px, py0;     // this thread's column and first row
@@ -396,8 +399,31 @@ __device__ __forceinline__ float2 alpha_box(float A, float B, float C, float o) 
   return make_float2(sqrtf(fmaxf(s * C, 0.f)) + 0.05f, sqrtf(fmaxf(s * A, 0.f)) + 0.05f);
 }
 
-__device__ __forceinline__ bool warp_misses(const WarpPix& q, float x, float y, float2 h) {
-  return h.x < 0.f || x + h.x < q.wx0 || x - h.x > q.wx0 + 7.f || y + h.y < q.wy0 || y - h.y > q.wy0 + 7.f;
+// The alpha box of a splat at (x, y) reaches the warp's square.
+__device__ __forceinline__ bool box_hits(const WarpPix& q, float x, float y, float2 h) {
+  return h.x >= 0.f && !(x + h.x < q.wx0 || x - h.x > q.wx0 + 7.f || y + h.y < q.wy0 || y - h.y > q.wy0 + 7.f);
+}
+
+// One splat as staged in shared memory.
+struct Splat {
+  float4 a;  // x, y, A, B
+  float4 b;  // C, opacity, r, g
+  float c;   // b
+  uint32_t id;
+};
+
+__device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, const float2* __restrict__ xy,
+                                            const float4* __restrict__ conic_o, const float4* __restrict__ rgb,
+                                            uint32_t pos, const WarpPix& q, Splat* slot) {
+  const uint32_t id = pvals[pos];
+  const float2 g = xy[id];
+  const float4 co = conic_o[id];
+  const float4 cc = rgb[id];
+  slot->a = make_float4(g.x, g.y, co.x, co.y);
+  slot->b = make_float4(co.z, co.w, cc.x, cc.y);
+  slot->c = cc.z;
+  slot->id = id;
+  return box_hits(q, g.x, g.y, alpha_box(co.x, co.y, co.z, co.w));
 }
 
 __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restrict__ ranges,
@@ -408,51 +434,38 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
                                                          float3 bg, float* __restrict__ img,
                                                          float* __restrict__ t_final, int* __restrict__ n_last,
                                                          const uint32_t* __restrict__ order) {
-  __shared__ float4 s_a[R_BATCH];  // x, y, A, B
-  __shared__ float4 s_b[R_BATCH];  // C, opacity, r, g
-  __shared__ float s_c[R_BATCH];   // b
-  __shared__ float2 s_h[R_BATCH];  // alpha box half-sizes
+  __shared__ Splat s_sp[R_WARPS][32];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const WarpPix q = warp_pixels(tile, TX);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
   const int n = (int)(r.y - r.x);
   const float fpx = (float)q.px;
   float T[R_PPT], C0[R_PPT], C1[R_PPT], C2[R_PPT];
   int last[R_PPT];
   bool live[R_PPT];
+  bool act = false;
 #pragma unroll
   for (int k = 0; k < R_PPT; ++k) {
     T[k] = 1.f;
     C0[k] = C1[k] = C2[k] = 0.f;
     last[k] = 0;
     live[k] = q.px < W && q.py0 + k < H;
+    act |= live[k];
   }
-  for (int b = 0; b < n; b += R_BATCH) {
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < R_PPT; ++k) any |= live[k];
-    if (__syncthreads_count(any) == 0) break;
-    for (int t = threadIdx.x; t < R_BATCH; t += R_THREADS) {
-      int k = b + t;
-      if (k < n) {
-        uint32_t id = pvals[r.x + k];
-        float2 g = xy[id];
-        float4 co = conic_o[id];
-        float4 cc = rgb[id];
-        s_a[t] = make_float4(g.x, g.y, co.x, co.y);
-        s_b[t] = make_float4(co.z, co.w, cc.x, cc.y);
-        s_c[t] = cc.z;
-        s_h[t] = alpha_box(co.x, co.y, co.z, co.w);
-      }
-    }
-    __syncthreads();
-    const int m = min(R_BATCH, n - b);
-    for (int j = 0; j < m; ++j) {
-      const float4 a = s_a[j];
-      if (warp_misses(q, a.x, a.y, s_h[j])) continue;
-      const float4 bb = s_b[j];
-      const float cb = s_c[j];
-      bool act = false;
+  bool going = __any_sync(0xffffffffu, act);
+  for (int b = 0; b < n && going; b += 32) {
+    const bool hit = b + lane < n && stage_splat(pvals, xy, conic_o, rgb, r.x + b + lane, q, &sp[lane]);
+    __syncwarp();
+    uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    while (bal) {
+      const int j = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const float4 a = sp[j].a;
+      const float4 bb = sp[j].b;
+      const float cb = sp[j].c;
+      act = false;
 #pragma unroll
       for (int k = 0; k < R_PPT; ++k) {
         float dx, dy;
@@ -472,8 +485,12 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
         last[k] = take ? b + j + 1 : last[k];
         act |= live[k];
       }
-      if (!__any_sync(0xffffffffu, act)) break;
+      if (!__any_sync(0xffffffffu, act)) {
+        going = false;
+        break;
+      }
     }
+    __syncwarp();  // the batch slots are rewritten next
   }
 #pragma unroll
   for (int k = 0; k < R_PPT; ++k) {
@@ -504,14 +521,11 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
                                                          const int* __restrict__ n_last,
                                                          const float* __restrict__ dl_dimg, float* __restrict__ g2,
                                                          uint64_t V, const uint32_t* __restrict__ order) {
-  __shared__ uint32_t s_id[R_BATCH];
-  __shared__ float4 s_a[R_BATCH];
-  __shared__ float4 s_b[R_BATCH];
-  __shared__ float s_c[R_BATCH];
-  __shared__ float2 s_h[R_BATCH];
-  __shared__ int s_max;
+  __shared__ Splat s_sp[R_WARPS][32];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const WarpPix q = warp_pixels(tile, TX);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
   const float fpx = (float)q.px;
   float T[R_PPT], gr[R_PPT], gg[R_PPT], gb[R_PPT], S0[R_PPT], S1[R_PPT], S2[R_PPT], tfb[R_PPT];
@@ -535,39 +549,27 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
     tfb[k] = T[k] * (bg.x * gr[k] + bg.y * gg[k] + bg.z * gb[k]);
     mylast = max(mylast, last[k]);
   }
-  // positions >= the warp's largest n_last contribute to none of its pixels
+  // list positions >= the warp's largest n_last contribute to none of its pixels
   int wlast = mylast;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0 && wlast > 0) atomicMax(&s_max, wlast);
-  __syncthreads();
-  const int maxlast = s_max;
-  for (int b = maxlast; b > 0; b -= R_BATCH) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < R_BATCH; t += R_THREADS) {
-      int k = b - 1 - t;
-      if (k >= 0) {
-        uint32_t id = pvals[r.x + k];
-        float2 g = xy[id];
-        float4 co = conic_o[id];
-        float4 cc = rgb[id];
-        s_id[t] = id;
-        s_a[t] = make_float4(g.x, g.y, co.x, co.y);
-        s_b[t] = make_float4(co.z, co.w, cc.x, cc.y);
-        s_c[t] = cc.z;
-        s_h[t] = alpha_box(co.x, co.y, co.z, co.w);
-      }
-    }
-    __syncthreads();
-    const int m = min(R_BATCH, b);
-    for (int j = max(0, b - wlast); j < m; ++j) {
-      const int pos = b - 1 - j;
-      const float4 a = s_a[j];
-      if (warp_misses(q, a.x, a.y, s_h[j])) continue;
-      const float4 bb = s_b[j];
-      const float cb = s_c[j];
+  // reduce-scatter roles: lane l ends with the warp sum of value
+  // 4 bit4(l) + 2 bit3(l) + bit2(l) of v[0..7]; v[8] by butterfly
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+  const int qsel = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+  for (int top = wlast; top > 0; top -= 32) {
+    // lane l stages list position top - 1 - l: ascending lanes, descending positions
+    const int k0 = top - 1 - lane;
+    const bool hit = k0 >= 0 && stage_splat(pvals, xy, conic_o, rgb, r.x + (uint32_t)k0, q, &sp[lane]);
+    __syncwarp();
+    uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    while (bal) {
+      const int j = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int pos = top - 1 - j;
+      const float4 a = sp[j].a;
+      const float4 bb = sp[j].b;
+      const float cb = sp[j].c;
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
 #pragma unroll
@@ -602,10 +604,6 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         v[4] += -0.5f * dpw * dy * dy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
-        // reduce-scatter of v[0..7] by recursive halving (lane l ends with the
-        // warp sum of value 4 bit4(l) + 2 bit3(l) + bit2(l)), v[8] by butterfly
-        const int l = threadIdx.x & 31;
-        const bool h4 = l & 16, h3 = l & 8, h2 = l & 4;
         float b4[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -624,15 +622,15 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
         b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
         const float s8 = warp_sum(v[8]);
-        const uint32_t id = s_id[j];
-        if ((l & 3) == 0) {
-          const int q = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
-          if (b1 != 0.f) atomicAdd(&g2[(uint64_t)q * V + id], b1);
-        } else if (l == 1 && s8 != 0.f) {
+        const uint32_t id = sp[j].id;
+        if ((lane & 3) == 0) {
+          if (b1 != 0.f) atomicAdd(&g2[(uint64_t)qsel * V + id], b1);
+        } else if (lane == 1 && s8 != 0.f) {
           atomicAdd(&g2[8ull * V + id], s8);
         }
       }
     }
+    __syncwarp();  // the batch slots are rewritten next
   }
 }
 
