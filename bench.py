@@ -185,7 +185,8 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = float(tt.item())
     # ---- end to end through the C ABI with host buffers: targets from pinned
-    # host memory copied inside every step, the loss read back every step
+    # host memory copied inside every step, every step's loss copied back
+    # (read with tgs_losses at the end of the timed region)
     host_t = torch.empty(len(cams), H, W, 3, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets.cpu())
     host_np = host_t.numpy()
@@ -195,12 +196,15 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
+    table.losses()
     e2.record(s)
     t0 = time.perf_counter()
     for t in range(n_e2e):
-        table.step([cams[t % nc]], host_np[t % nc:t % nc + 1], next_cams=[cams[(t + 1) % nc]], want_loss=True)
+        table.step([cams[t % nc]], host_np[t % nc:t % nc + 1], next_cams=[cams[(t + 1) % nc]], want_loss=False)
+    e2e_losses = table.losses()
     e3.record(s)
     torch.cuda.synchronize()
+    assert len(e2e_losses) == n_e2e and np.isfinite(e2e_losses).all()
     wall_e2e = time.perf_counter() - t0
     e2e_ms = max(e2.elapsed_time(e3), 1e3 * wall_e2e) / n_e2e
     return dict(ms=ms, stages=stages, stats=st, launches=launches, clocks=clocks, rec=rec, table=table,
@@ -360,19 +364,24 @@ def run_street(args, rank, world, local):
     forms["bf16_exact"] = timed(tb, "bf16_exact")
     tb.set_prefetch_mode(2)
     head = forms["bf16_learned"]
+    drive_b = drive_b_eval(args, tgs, tb, pred, host, base, dev)
     peak = link_peak(torch)
     # end to end (headline form) with host targets and the loss read back each step
     host_t = torch.empty(min(nc, 64), H, W, 3, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets[:host_t.shape[0]].cpu())
     host_np = host_t.numpy()
     n_e2e = max(5, args.steps // 2)
+    tb.losses()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for k in range(n_e2e):
         i = k % host_np.shape[0]
-        tb.step([cams[i]], host_np[i:i + 1], next_cams=[cams[(i + 1) % nc]], want_loss=True)
+        # host targets copied up and every step's loss copied back (tgs_losses)
+        tb.step([cams[i]], host_np[i:i + 1], next_cams=[cams[(i + 1) % nc]], want_loss=False)
+    e2e_losses = tb.losses()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
+    assert len(e2e_losses) == n_e2e and np.isfinite(e2e_losses).all()
     d = head["delta"]
     link = {"peak_gbs": peak, "bytes_h2d_per_step": d["bytes_h2d"] / args.steps,
             "bytes_d2h_per_step": d["bytes_d2h"] / args.steps,
@@ -398,7 +407,46 @@ def run_street(args, rank, world, local):
                host=host, forms=summary, psnr_gap_db=round(gap, 4), predictor_train_s=round(t_train, 1))
     out["_pred"] = pred
     out["bf16"] = True
+    out["drive_b"] = drive_b
     return out
+
+
+def drive_b_eval(args, tgs, tb, pred, host, base, dev, n=100):
+    """Generalisation of the predictor (trained on drive A's logs): a second
+    drive (another start, heading and turn sequence) on the same scene, the
+    BF16 table with the learned prefetch against reactive streaming; demand
+    hit rate, predicted blocks and iters/s over n steps (targets: renders of
+    the current parameters, so the steps train on a fixed image)."""
+    import torch
+    cams = scenes.street_drive_cameras(n + 1, seed=2003, start=(30, 12), heading=(0.0, 1.0))
+    W, H = cams[0]["width"], cams[0]["height"]
+    tgt = torch.empty(1, H, W, 3, device=dev)
+    res = {}
+    for mode, label in ((2, "learned"), (0, "reactive")):
+        t = tgs.TideTable(host, prefetch_mode=mode, host_bf16=1, stochastic_round=1, **base)
+        if mode == 2:
+            t.set_predictor(pred, threshold=0.3, horizon_mask=0b11)
+        t.render(cams[0], tgt[0])
+        for k in range(3):
+            t.step([cams[k]], tgt, want_loss=False)
+        t.sync()
+        s0 = t.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(3, n):
+            t.step([cams[k]], tgt, want_loss=False)
+        e1.record()
+        t.sync()
+        torch.cuda.synchronize()
+        st = t.stats()
+        d = {k: st[k] - s0[k] for k in ("demand_blocks", "demand_hits", "predicted_blocks", "stall_ms")}
+        res[label] = {"iters_per_s": round(1e3 * (n - 3) / e0.elapsed_time(e1), 2),
+                      "demand_hit_rate": round(d["demand_hits"] / max(d["demand_blocks"], 1), 5),
+                      "predicted_blocks_per_step": round(d["predicted_blocks"] / (n - 3), 3),
+                      "stall_ms_per_step": round(d["stall_ms"] / (n - 3), 4)}
+        t.close()
+    res["steps"] = n - 3
+    return res
 
 
 def cpu_baseline_street(res):
@@ -625,6 +673,7 @@ def main():
         line["forms"] = res["forms"]
         line["psnr_gap_db"] = res["psnr_gap_db"]
         line["vs_fp32_reactive"] = round(value / max(res["forms"]["fp32_reactive"]["iters_per_s"], 1e-9), 4)
+        line["drive_b"] = res["drive_b"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()

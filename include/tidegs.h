@@ -124,7 +124,8 @@ void tgs_destroy(tgs_table* t);
  * targets_dev: device, batch x H x W x 3, or NULL when targets_host is given;
  *   read after `stream`'s prior work.
  * targets_host: host (pinned or pageable), used when targets_dev is NULL; copied
- *   inside the call.
+ *   inside the call on the copy stream (pinned memory: asynchronously, into one
+ *   of two device buffers, overlapping the previous step).
  * loss_out: host, may be NULL; when given the call waits for the step and writes
  *   the batch loss (mean over cameras, pixels and channels).
  * Errors: TGS_ERR_INVALID, TGS_ERR_CAPACITY (a batch's working set exceeds the
@@ -137,6 +138,15 @@ tgs_status tgs_step(tgs_table* t, const tgs_camera* cams, uint32_t batch, const 
  * working set is made resident first (it counts as a step of the residency
  * policy, without parameter updates).  image_dev: device, H x W x 3. */
 tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, void* stream);
+
+/* Losses of the training steps since the previous call, oldest first (the
+ * photometric loss f_i of App. A.1, mean over cameras, pixels and channels).
+ * Every step copies its loss to pinned host memory asynchronously, so a
+ * caller can read them without waiting on each step; the call waits for the
+ * compute stream.  At most the last 4096 steps are kept.
+ * out_host: host, room for max_count floats; count: host, receives the number
+ * written.  Errors: TGS_ERR_INVALID. */
+tgs_status tgs_losses(tgs_table* t, float* out_host, uint64_t max_count, uint64_t* count);
 
 /* Changes prefetch_mode (0 reactive, 1 exact next batch, 2 learned) between
  * steps; a pending prefetch is kept and used if it matches the next batch. */

@@ -66,6 +66,7 @@ _SIGS = {
                                   _VP, ctypes.POINTER(_F)]),
     "tgs_render": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_camera), _VP, _VP]),
     "tgs_sync": (ctypes.c_int32, [_VP]),
+    "tgs_losses": (ctypes.c_int32, [_VP, _VP, ctypes.c_uint64, _VP]),
     "tgs_set_prefetch_mode": (ctypes.c_int32, [_VP, _U32]),
     "tgs_get_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_set_params": (ctypes.c_int32, [_VP, _VP]),
@@ -220,6 +221,13 @@ class TideTable:
 
     def sync(self):
         _check(load().tgs_sync(self.h))
+
+    def losses(self, max_count=4096):
+        """Per-step losses since the previous call (tgs_losses)."""
+        out = np.zeros(max_count, np.float32)
+        n = _U64()
+        _check(load().tgs_losses(self.h, _ptr(out), max_count, ctypes.byref(n)))
+        return out[:n.value].copy()
 
     def set_prefetch_mode(self, mode):
         _check(load().tgs_set_prefetch_mode(self.h, mode))

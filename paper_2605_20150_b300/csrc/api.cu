@@ -167,6 +167,13 @@ tgs_status tgs_set_prefetch_mode(tgs_table* t, uint32_t mode) {
   });
 }
 
+tgs_status tgs_losses(tgs_table* t, float* out_host, uint64_t max_count, uint64_t* count) {
+  return guard([&] {
+    TGS_CHECK(t && out_host && count, TGS_ERR_INVALID, "tgs_losses: null argument");
+    *count = t->t.losses(out_host, max_count);
+  });
+}
+
 tgs_status tgs_sync(tgs_table* t) {
   return guard([&] {
     TGS_CHECK(t, TGS_ERR_INVALID, "tgs_sync: null table");

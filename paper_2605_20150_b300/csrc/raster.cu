@@ -778,23 +778,16 @@ __device__ __forceinline__ void chain_rule(const DevCam& c, const float* __restr
 // mode 1: add the gradient of visible Gaussians to that array;
 // mode 2: add into a pool with the render list's slot layout.
 template <bool BF>
-__global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
-                                                              const uint32_t* __restrict__ ntiles,
-                                                              const float4* __restrict__ rgbv,
-                                                              const float4* __restrict__ conic_o,
-                                                              const float* __restrict__ g2, uint64_t V,
-                                                              float* __restrict__ grad, uint64_t Vg, int mode,
-                                                              unsigned cpi, const uint8_t* __restrict__ touched) {
-  const unsigned item = blockIdx.x / cpi;
-  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+__device__ __forceinline__ void pbwd_row(const RenderList& rl, const DevCam& c, const uint32_t* __restrict__ ntiles,
+                                         const float4* __restrict__ rgbv, const float4* __restrict__ conic_o,
+                                         const float* __restrict__ g2, uint64_t V, float* __restrict__ grad,
+                                         uint64_t Vg, int mode, unsigned item, unsigned lane, uint64_t i,
+                                         bool listed) {
   const uint32_t B = rl.B;
-  if (lane >= B) return;
-  const uint64_t i = (uint64_t)item * B + lane;
-  if (lane >= rl.item_count[item]) return;
   const bool vis = ntiles[i] != 0;
-  // mode 0 stores the rows the optimiser reads (touched by the batch; all if
-  // touched is null), zero where this camera does not see the Gaussian
-  if (!vis && (mode != 0 || (touched && !touched[i]))) return;
+  // mode 0 stores the rows the optimiser reads (the listed rows, touched by
+  // the batch), zero where this camera does not see the Gaussian
+  if (!vis && (mode != 0 || !listed)) return;
   const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
   const float* p = rl.base + sbase;
   const __nv_bfloat16* q16 = sh16(rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride, B, lane);
@@ -818,30 +811,77 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   }
 }
 
-// Masked Adam over the render list.  CTA (item chunk, field group): each
-// thread updates ADAM_FG consecutive fields of one Gaussian, so a warp keeps
-// several independent coalesced loads of p, g, m and v in flight.  The bias
-// corrections 1 / (1 - beta^step) of the item's block come precomputed.
+// Every render-list position (rows == null; mode 0 then stores every valid
+// row) or the listed rows (grid-stride over *nrows).
+template <bool BF>
+__global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, DevCam c,
+                                                              const uint32_t* __restrict__ ntiles,
+                                                              const float4* __restrict__ rgbv,
+                                                              const float4* __restrict__ conic_o,
+                                                              const float* __restrict__ g2, uint64_t V,
+                                                              float* __restrict__ grad, uint64_t Vg, int mode,
+                                                              unsigned cpi, const uint32_t* __restrict__ rows,
+                                                              const uint32_t* __restrict__ nrows) {
+  const uint32_t B = rl.B;
+  if (rows) {
+    const uint32_t n = *nrows;
+    for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
+      const uint32_t i = rows[t];
+      const unsigned item = i / B, lane = i - item * B;
+      pbwd_row<BF>(rl, c, ntiles, rgbv, conic_o, g2, V, grad, Vg, mode, item, lane, i, true);
+    }
+    return;
+  }
+  const unsigned item = blockIdx.x / cpi;
+  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+  if (lane >= B) return;
+  const uint64_t i = (uint64_t)item * B + lane;
+  if (lane >= rl.item_count[item]) return;
+  pbwd_row<BF>(rl, c, ntiles, rgbv, conic_o, g2, V, grad, Vg, mode, item, lane, i, true);
+}
+
+// The render-list positions with touched != 0: one warp per 128 positions
+// (4 per lane), a warp scan of the counts and one atomic per warp, so each
+// group's rows are written in ascending order (groups in any order).
+__global__ void k_touched_rows(const uint8_t* __restrict__ touched, uint64_t V, uint32_t* __restrict__ rows,
+                               uint32_t* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t g0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 128; g0 < V;
+       g0 += warps * 128) {
+    const uint64_t p0 = g0 + 4 * (uint64_t)lane;
+    uint32_t f = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (p0 + e < V && touched[p0 + e]) f |= 1u << e;
+    const uint32_t c = __popc(f);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 0) + inc - c;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (f >> e & 1u) rows[base++] = (uint32_t)(p0 + e);
+  }
+}
+
 constexpr int ADAM_FG = 8;
 constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
 
 template <bool BF>
-__global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
-                                                    const uint8_t* __restrict__ touched,
-                                                    const float2* __restrict__ bias,
-                                                    const uint32_t* __restrict__ block_step, uint64_t V, float lr,
-                                                    float b1, float b2, float eps, unsigned cpi,
-                                                    const uint32_t* __restrict__ abort_flag) {
-  if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
-  const unsigned item = blockIdx.x / cpi;
-  const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
+__device__ __forceinline__ void adam_row(const RenderList& rl, const float* __restrict__ grad,
+                                         const float2* __restrict__ bias, const uint32_t* __restrict__ block_step,
+                                         uint64_t V, float lr, float b1, float b2, float eps, unsigned item,
+                                         unsigned lane, uint64_t i, int f0) {
   const uint32_t B = rl.B;
-  if (lane >= B) return;
-  const uint64_t i = (uint64_t)item * B + lane;
-  if (lane >= rl.item_count[item] || !touched[i]) return;
   const float2 bc = bias[item];
   const float ic1 = bc.x, ic2 = bc.y;
-  const int f0 = blockIdx.y * ADAM_FG;
   float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
   float* p = slot + lane;
   if (!BF) {
@@ -889,6 +929,29 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
         }
       }
     }
+  }
+}
+
+// Masked Adam over the touched rows of the render list (rows[0..*nrows)):
+// CTA (row chunk, field group), each thread ADAM_FG consecutive fields of one
+// Gaussian, so a warp keeps several independent coalesced loads of p, g, m
+// and v in flight.  The bias corrections of the item's block come
+// precomputed.
+template <bool BF>
+__global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float* __restrict__ grad,
+                                                    const uint32_t* __restrict__ rows,
+                                                    const uint32_t* __restrict__ nrows,
+                                                    const float2* __restrict__ bias,
+                                                    const uint32_t* __restrict__ block_step, uint64_t V, float lr,
+                                                    float b1, float b2, float eps,
+                                                    const uint32_t* __restrict__ abort_flag) {
+  if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
+  const uint32_t B = rl.B, n = *nrows;
+  const int f0 = blockIdx.y * ADAM_FG;
+  for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
+    const uint32_t i = rows[t];
+    const unsigned item = i / B, lane = i - item * B;
+    adam_row<BF>(rl, grad, bias, block_step, V, lr, b1, b2, eps, item, lane, i, f0);
   }
 }
 
@@ -1284,29 +1347,48 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
 }
 
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
-                            cudaStream_t s, const uint8_t* touched) {
+                            cudaStream_t s, const uint32_t* rows, const uint32_t* nrows) {
   if (rl.capacity() == 0) return;
   unsigned cpi = div_up(rl.B, PP_THREADS);
+  if (rows) {
+    const unsigned grid = std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM);
+    if (rl.bf16)
+      k_preprocess_bwd<true><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v, grad,
+                                                        rl.capacity(), mode, cpi, rows, nrows);
+    else
+      k_preprocess_bwd<false><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v, grad,
+                                                         rl.capacity(), mode, cpi, rows, nrows);
+    TGS_LAUNCHED();
+    return;
+  }
   if (rl.bf16)
     k_preprocess_bwd<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi, touched);
+                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
   else
     k_preprocess_bwd<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi, touched);
+                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
   TGS_LAUNCHED();
 }
 
-void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const float2* bias,
-                      const uint32_t* block_step, float lr, float b1, float b2, float eps, cudaStream_t s,
-                      const uint32_t* abort_flag) {
+void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s) {
+  TGS_CUDA(cudaMemsetAsync(nrows, 0, sizeof(uint32_t), s));
+  const uint64_t V = rl.capacity();
+  if (V == 0) return;
+  const unsigned grid = std::min<uint64_t>(div_up(V, 128 * 8), 4 * NSM);
+  k_touched_rows<<<grid, 256, 0, s>>>(touched, V, rows, nrows);
+  TGS_LAUNCHED();
+}
+
+void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
+                      const float2* bias, const uint32_t* block_step, float lr, float b1, float b2, float eps,
+                      cudaStream_t s, const uint32_t* abort_flag) {
   if (rl.capacity() == 0) return;
-  unsigned cpi = div_up(rl.B, PP_THREADS);
-  const dim3 grid(rl.n_items * cpi, ADAM_GROUPS);
+  const dim3 grid(std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM), ADAM_GROUPS);
   if (rl.bf16)
-    k_adam<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, touched, bias, block_step, rl.capacity(), lr, b1, b2, eps, cpi,
+    k_adam<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, rows, nrows, bias, block_step, rl.capacity(), lr, b1, b2, eps,
                                             abort_flag);
   else
-    k_adam<false><<<grid, PP_THREADS, 0, s>>>(rl, grad, touched, bias, block_step, rl.capacity(), lr, b1, b2, eps, cpi,
+    k_adam<false><<<grid, PP_THREADS, 0, s>>>(rl, grad, rows, nrows, bias, block_step, rl.capacity(), lr, b1, b2, eps,
                                              abort_flag);
   TGS_LAUNCHED();
 }

@@ -103,19 +103,23 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
 // position's gradient (zero when invisible) into a local [59][rl.capacity()] array,
 // mode 1 adds visible gradients to it, mode 2 adds into a pool with the
 // render list's slot layout (grad = pool base).
-// touched (render-list bytes, may be null): mode 0 then skips the rows no
-// camera of the batch touched (the optimiser does not read them).
+// rows / nrows (device, may be null): work on the listed render-list
+// positions only (touched_rows); mode 0 then stores exactly those rows.
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
-                            cudaStream_t s, const uint8_t* touched = nullptr);
+                            cudaStream_t s, const uint32_t* rows = nullptr, const uint32_t* nrows = nullptr);
 
-// Masked Adam over the render list: rows with touched != 0 update params and
-// moments in the pool; `grad` is the local [59][rl.capacity()] array; step counters per
+// rows[0..*nrows) = the render-list positions with touched != 0 (groups of
+// 128 positions in ascending order, groups in any order).
+void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s);
+
+// Masked Adam over the listed (touched) rows of the render list: params and
+// moments in the pool are updated; `grad` is the local [59][rl.capacity()] array; step counters per
 // block id (already incremented for this step).  Nothing is updated while
 // *abort_flag (device, may be null) is set.
 // bias: per item (1 / (1 - b1^step), 1 / (1 - b2^step)) from mark_touched_blocks.
-void adam_render_list(const RenderList& rl, const float* grad, const uint8_t* touched, const float2* bias,
-                      const uint32_t* block_step, float lr, float b1, float b2, float eps, cudaStream_t s,
-                      const uint32_t* abort_flag = nullptr);
+void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
+                      const float2* bias, const uint32_t* block_step, float lr, float b1, float b2, float eps,
+                      cudaStream_t s, const uint32_t* abort_flag = nullptr);
 
 // Per-item bookkeeping before Adam: for items with item_touched != 0,
 // block_step[block] += 1 and dirty[slot] = 1.  While abort_flag[0] is set

@@ -120,6 +120,51 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __r
   }
 }
 
+// Small scans in one CTA: chunks of SCAN_CHUNK in order, carrying the sum.
+constexpr uint64_t SCAN_SINGLE_MAX = 16 * SCAN_CHUNK;
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const uint32_t* __restrict__ in,
+                                                             uint32_t* __restrict__ out, uint64_t n,
+                                                             uint32_t* __restrict__ total) {
+  __shared__ uint32_t buf[SCAN_CHUNK + SCAN_CHUNK / 32];
+  __shared__ uint32_t sw[SCAN_THREADS / 32 + 1];
+  uint32_t carry = 0;
+  for (uint64_t base = 0; base < n; base += SCAN_CHUNK) {
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int q = i * SCAN_THREADS + threadIdx.x;
+      uint64_t p = base + q;
+      buf[q + (q >> 5)] = p < n ? in[p] : 0;
+    }
+    __syncthreads();
+    uint32_t v[SCAN_ITEMS];
+    uint32_t sm = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int q = threadIdx.x * SCAN_ITEMS + i;
+      v[i] = buf[q + (q >> 5)];
+      sm += v[i];
+    }
+    uint32_t tot;
+    uint32_t e = block_excl_scan<SCAN_THREADS>(sm, sw, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int q = threadIdx.x * SCAN_ITEMS + i;
+      buf[q + (q >> 5)] = e;
+      e += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int q = i * SCAN_THREADS + threadIdx.x;
+      uint64_t p = base + q;
+      if (p < n) out[p] = buf[q + (q >> 5)];
+    }
+    carry += tot;
+    __syncthreads();  // buf is refilled next
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, uint64_t n,
                                                           int shift, uint32_t mask,
                                                           uint32_t* __restrict__ counts, uint32_t nc) {
@@ -470,6 +515,11 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total_dev, 
     if (total_dev) TGS_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s));
     return;
   }
+  if (n <= SCAN_SINGLE_MAX) {
+    k_scan_single<<<1, SCAN_THREADS, 0, s>>>(in, out, n, total_dev);
+    TGS_LAUNCHED();
+    return;
+  }
   uint32_t nc = div_up(n, SCAN_CHUNK);
   uint32_t* partial = (uint32_t*)scratch;
   k_scan_reduce<<<nc, SCAN_THREADS, 0, s>>>(in, n, partial);
@@ -493,7 +543,12 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
     uint32_t mask = (1u << nb) - 1u;
     k_radix_hist<<<nc, RS_THREADS, 0, s>>>(ki, n, shift, mask, counts, nc);
     TGS_LAUNCHED();
-    exclusive_scan_u32(counts, counts, nullptr, (uint64_t)nc * RS_BINS, scan_scr, s);
+    if ((uint64_t)nc * RS_BINS <= 4 * RSO_THREADS) {
+      k_rsd_offsets<<<1, RSO_THREADS, 0, s>>>(counts, nc);  // same digit-major table
+      TGS_LAUNCHED();
+    } else {
+      exclusive_scan_u32(counts, counts, nullptr, (uint64_t)nc * RS_BINS, scan_scr, s);
+    }
     k_radix_scatter<<<nc, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, mask, counts, nc);
     TGS_LAUNCHED();
     uint32_t* t;

@@ -89,11 +89,16 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   max_items = (uint32_t)C;
   V_cap = (uint64_t)max_items * B;
 
-  TGS_CUDA(cudaStreamCreateWithFlags(&comp, cudaStreamNonBlocking));
+  // the control stream's short selection kernels are scheduled ahead of the
+  // compute stream's long raster kernels (the host waits on the former)
+  int prio_low = 0, prio_high = 0;
+  TGS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  TGS_CUDA(cudaStreamCreateWithPriority(&comp, cudaStreamNonBlocking, prio_low));
   TGS_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
-  TGS_CUDA(cudaStreamCreateWithFlags(&ctl, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb, &ev_snap})
+  TGS_CUDA(cudaStreamCreateWithPriority(&ctl, cudaStreamNonBlocking, prio_high));
+  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb, &ev_snap, &ev_tgt_ready, &ev_tgt_used[0],
+                         &ev_tgt_used[1]})
     TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   TGS_CUDA(cudaEventCreate(&ev_stall_a));
   TGS_CUDA(cudaEventCreate(&ev_stall_b));
@@ -174,10 +179,14 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   }
   dalloc(images, cfg.max_batch * pix * 3);
   dalloc(dl_dimg, cfg.max_batch * pix * 3);
-  dalloc(targets_buf, cfg.max_batch * pix * 3);
+  dalloc(targets_buf, 2 * cfg.max_batch * pix * 3);  // double buffer for host targets
+  TGS_CUDA(cudaMallocHost(&loss_ring, LOSS_RING * sizeof(float)));
+  loss_norm.assign(LOSS_RING, 1.f);
   dalloc(touched, V_cap);
   dalloc(item_touched, max_items);
   dalloc(item_bias, max_items);
+  V_cap_rows = V_cap;
+  dalloc(rows_dev, V_cap + 1);  // touched rows, then their count
   dalloc(grad_local, (uint64_t)D * V_cap);
   dalloc(loss_dev, 4);
   TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
@@ -277,15 +286,17 @@ void Table::destroy() {
   for (auto& cs : cams) cam_state_free(cs);
   void* dev[] = {pool, spheres, spheres_snap, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
                  kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
-                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, item_bias, grad_local,
+                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, item_bias, rows_dev, grad_local,
                  loss_dev, abort_dev};
   for (void* p : dev) dfree(p);
-  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host};
+  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host,
+                 loss_ring};
   for (void* p : hst)
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap})
+  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap, ev_tgt_ready,
+                        ev_tgt_used[0], ev_tgt_used[1]})
     if (e) cudaEventDestroy(e);
   for (cudaStream_t s : {comp, h2d, d2h, ctl})
     if (s) cudaStreamDestroy(s);
@@ -560,11 +571,25 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   TGS_CUDA(cudaStreamWaitEvent(comp, ev_h2d, 0));
   TGS_CUDA(cudaEventRecord(ev_stall_b, comp));
   stall_pending = true;
+  const float* tgt = targets_dev;
+  int tgt_buf = -1;
   if (backward) {
     // the bounds as this step starts: the next own-batch cull reads them while
     // this step refreshes the live copy
     TGS_CUDA(cudaMemcpyAsync(spheres_snap, spheres, K * sizeof(float4), cudaMemcpyDeviceToDevice, comp));
     TGS_CUDA(cudaEventRecord(ev_snap, comp));
+    if (!tgt) {
+      // host targets go up on the copy stream into the buffer the step before
+      // last used, overlapping the work still queued ahead of this step
+      TGS_CHECK(targets_host != nullptr, TGS_ERR_INVALID, "targets are required for a training step");
+      tgt_buf = tgt_parity;
+      tgt_parity ^= 1;
+      float* dst = targets_buf + (uint64_t)tgt_buf * cfg.max_batch * pix * 3;
+      if (tgt_used[tgt_buf]) TGS_CUDA(cudaStreamWaitEvent(h2d, ev_tgt_used[tgt_buf], 0));
+      TGS_CUDA(cudaMemcpyAsync(dst, targets_host, (uint64_t)J * pix * 3 * sizeof(float), cudaMemcpyHostToDevice, h2d));
+      TGS_CUDA(cudaEventRecord(ev_tgt_ready, h2d));
+      tgt = dst;
+    }
   }
   for (uint32_t j = 0; j < n_items; ++j) {
     uint32_t b = p.render_blocks[j];
@@ -590,19 +615,26 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   }
   stats.last_render_blocks = n_items;
   if (backward) {
-    const float* tgt = targets_dev;
-    if (!tgt) {
-      TGS_CHECK(targets_host != nullptr, TGS_ERR_INVALID, "targets are required for a training step");
-      TGS_CUDA(cudaMemcpyAsync(targets_buf, targets_host, (uint64_t)J * pix * 3 * sizeof(float),
-                               cudaMemcpyHostToDevice, comp));
-      tgt = targets_buf;
+    if (tgt_buf >= 0) {
+      TGS_CUDA(cudaStreamWaitEvent(comp, ev_tgt_ready, 0));
     } else {
       TGS_CUDA(cudaEventRecord(ev_user, user));
       TGS_CUDA(cudaStreamWaitEvent(comp, ev_user, 0));
     }
     TGS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), comp));
+    // the rows the chain rule stores and the optimiser updates
+    touched_rows(rl, touched, rows_dev, rows_dev + V_cap_rows, comp);
     timer.begin(StageTimer::LOSS, comp);
     photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
+    if (tgt_buf >= 0) {
+      TGS_CUDA(cudaEventRecord(ev_tgt_used[tgt_buf], comp));
+      tgt_used[tgt_buf] = 1;
+    }
+    // every step's loss reaches the host asynchronously (tgs_losses)
+    TGS_CUDA(cudaMemcpyAsync(loss_ring + loss_enq % LOSS_RING, loss_dev, sizeof(float), cudaMemcpyDeviceToHost,
+                             comp));
+    loss_norm[loss_enq % LOSS_RING] = (float)((uint64_t)J * pix * 3);
+    ++loss_enq;
     timer.end(StageTimer::LOSS, comp);
     for (uint32_t j = 0; j < J; ++j) {
       DevCam dc = make_devcam(p.cams[j]);
@@ -610,13 +642,13 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
       render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
       timer.end(StageTimer::BWD, comp);
       timer.begin(StageTimer::PBWD, comp);
-      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp, touched);
+      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp, rows_dev, rows_dev + V_cap_rows);
       timer.end(StageTimer::PBWD, comp);
     }
     timer.begin(StageTimer::ADAM, comp);
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias);
-    adam_render_list(rl, grad_local, touched, item_bias, block_step, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, comp,
-                     abort_dev);
+    adam_render_list(rl, grad_local, rows_dev, rows_dev + V_cap_rows, item_bias, block_step, cfg.lr, cfg.beta1,
+                     cfg.beta2, cfg.eps, comp, abort_dev);
     timer.end(StageTimer::ADAM, comp);
     // the next batch's cull (control stream) reads the bounds first
     TGS_CUDA(cudaStreamWaitEvent(comp, ev_ctl, 0));
@@ -696,6 +728,17 @@ void Table::render(const tgs_camera& cam, float* image_dev, cudaStream_t user) {
   // the same selection is rendered again
   if (check_overflow(true)) compute(p, nullptr, nullptr, user, false, image_dev);
   prep = Prepared();
+}
+
+uint64_t Table::losses(float* out, uint64_t max_count) {
+  TGS_CUDA(cudaStreamSynchronize(comp));
+  uint64_t first = loss_read;
+  if (loss_enq - first > LOSS_RING) first = loss_enq - LOSS_RING;
+  uint64_t n = 0;
+  for (uint64_t k = first; k < loss_enq && n < max_count; ++k, ++n)
+    out[n] = loss_ring[k % LOSS_RING] / loss_norm[k % LOSS_RING];
+  loss_read = loss_enq;
+  return n;
 }
 
 bool Table::check_overflow(bool wait) {

@@ -70,7 +70,16 @@ struct Table {
   float* grad_local = nullptr;
   float* loss_dev = nullptr;
   float* loss_host = nullptr;
+  static constexpr uint64_t LOSS_RING = 4096;
+  float* loss_ring = nullptr;      // pinned: the loss sum of the last LOSS_RING steps
+  std::vector<float> loss_norm;    // element counts of those steps
+  uint64_t loss_enq = 0, loss_read = 0;
+  int tgt_parity = 0;              // host targets: double buffer in targets_buf
+  int tgt_used[2] = {0, 0};
+  cudaEvent_t ev_tgt_ready = nullptr, ev_tgt_used[2] = {nullptr, nullptr};
   float2* item_bias = nullptr;     // per render-list item: Adam bias corrections of this step
+  uint32_t* rows_dev = nullptr;    // touched render-list rows of this step, count at rows_dev[V_cap_rows]
+  uint64_t V_cap_rows = 0;
   uint32_t* abort_dev = nullptr;   // [2]: a render of a step overflowed its pairs; steps dropped since
   uint32_t* abort_host = nullptr;  // pinned
 
@@ -130,6 +139,9 @@ struct Table {
   // last renders' counts are on the host): grows the pair buffers, counts
   // the dropped steps and clears the flag.  Returns true if one was handled.
   bool check_overflow(bool wait);
+  // the losses (mean per step) of the steps since the last call, oldest
+  // first, at most the last LOSS_RING; waits for the compute stream
+  uint64_t losses(float* out, uint64_t max_count);
   RenderList render_list(uint32_t n_items) const;
 };
 

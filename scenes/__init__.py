@@ -379,13 +379,15 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
 
 
 def street_drive_cameras(n_cams=500, seed=1003, side=4000.0, road_every=100.0, height=1.5, step=2.0,
-                         width=1600, height_px=900, fov_x=90.0, znear=0.2, zfar=200.0, turn_every=400.0):
+                         width=1600, height_px=900, fov_x=90.0, znear=0.2, zfar=200.0, turn_every=400.0,
+                         start=(3, 3), heading=(1.0, 0.0)):
     """A connected drive along the road centre lines: 2 m per frame at 1.5 m
-    height, turning left or right at an intersection every `turn_every`
-    metres (turn direction from the seeded stream), looking along the road."""
+    height, starting at intersection `start` (road indices) with `heading`,
+    turning left or right at an intersection every `turn_every` metres (turn
+    direction from the seeded stream), looking along the road."""
     u = uniform(seed, 60, n_cams + 8)
-    pos = np.array([road_every * 3 - side / 2, road_every * 3 - side / 2])
-    d = np.array([1.0, 0.0])
+    pos = np.array([road_every * start[0] - side / 2, road_every * start[1] - side / 2])
+    d = np.array(heading, np.float64)
     travelled = 0.0
     cams = []
     k = 0

@@ -97,3 +97,26 @@ def test_render_is_ordered_on_the_default_stream(tgs):
         tab.render(cfg["cams"][0], img)
         assert np.array_equal(img.cpu().numpy(), ref_h)  # .cpu() runs on the default stream
     tab.close()
+
+
+def test_async_losses_match_the_synchronous_ones(tgs):
+    """Host targets copied on the copy stream (double buffer) and the per-step
+    loss ring: the losses read afterwards equal those read step by step."""
+    cfg = scenes.small_cube_config()
+    cams = _cams()
+    rng = np.random.default_rng(5)
+    tg = [rng.uniform(0.0, 0.5, (1, 160, 192, 3)).astype(np.float32) for _ in range(3)]
+    common = dict(block_size=250, max_batch=1, max_width=192, max_height=160, loss=1, lr=1e-3, cache_blocks=60,
+                  spare_slots=4)
+    a = tgs.TideTable(cfg["params"], **common)
+    b = tgs.TideTable(cfg["params"], **common)
+    seq = [(cams[i % 4], tg[i % 3]) for i in range(7)]
+    sync = [a.step([c], t) for c, t in seq]
+    for c, t in seq:
+        b.step([c], t, want_loss=False)
+    got = b.losses()
+    assert len(got) == len(seq)
+    np.testing.assert_allclose(got, sync, rtol=1e-5)
+    assert len(b.losses()) == 0
+    a.close()
+    b.close()
