@@ -125,7 +125,9 @@ void tgs_destroy(tgs_table* t);
  *   read after `stream`'s prior work.
  * targets_host: host (pinned or pageable), used when targets_dev is NULL; copied
  *   inside the call on the copy stream (pinned memory: asynchronously, into one
- *   of two device buffers, overlapping the previous step).
+ *   of two device buffers, overlapping the previous step; pinned targets must
+ *   then stay unchanged until the step has run, e.g. until tgs_sync or a later
+ *   step's loss is read).
  * loss_out: host, may be NULL; when given the call waits for the step and writes
  *   the batch loss (mean over cameras, pixels and channels).
  * Errors: TGS_ERR_INVALID, TGS_ERR_CAPACITY (a batch's working set exceeds the

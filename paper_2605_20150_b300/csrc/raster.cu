@@ -275,6 +275,23 @@ __global__ void k_gather_counts(const uint32_t* __restrict__ nv_dev, const uint3
 constexpr int EP_THREADS = 256;
 constexpr int EP_CHUNK = 1024;
 
+// Warp-cooperative form of last_le: each round the 32 lanes probe 32 evenly
+// spaced entries and the range shrinks to one gap.
+__device__ __forceinline__ uint32_t warp_last_le(const uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 32) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t pv = lo + lane * step;
+    const uint32_t b = __ballot_sync(0xffffffffu, pv < hi && a[pv] <= x);
+    const uint32_t L = 31 - __clz(b);  // lane 0 always qualifies (a[lo] <= x)
+    lo += L * step;
+    hi = min(hi, lo + step);
+  }
+  const uint32_t b = __ballot_sync(0xffffffffu, lo + lane < hi && a[lo + lane] <= x);
+  return lo + (31 - __clz(b));
+}
+
 __device__ __forceinline__ uint32_t last_le(const uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
   // largest i < n with a[i] <= x (a non-decreasing, a[0] <= x)
   uint32_t lo = 0, hi = n;
@@ -306,11 +323,14 @@ __global__ void __launch_bounds__(EP_THREADS) k_emit_pairs(const uint32_t* __res
   }
   for (uint32_t p0 = blockIdx.x * EP_CHUNK; p0 < np; p0 += gridDim.x * EP_CHUNK) {
     const uint32_t p1 = min(p0 + EP_CHUNK, np) - 1;
-    if (threadIdx.x == 0) {
-      const uint32_t lo = last_le(off, nv, p0), hi = last_le(off, nv, p1);
-      s_lo = lo;
-      s_cnt = hi - lo + 1;
+    // warp 0 finds the chunk's first Gaussian, warp 1 its last
+    if (threadIdx.x < 64) {
+      const uint32_t k = warp_last_le(off, nv, threadIdx.x < 32 ? p0 : p1);
+      if (threadIdx.x == 0) s_lo = k;
+      if (threadIdx.x == 32) s_cnt = k;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s_cnt = s_cnt - s_lo + 1;
     __syncthreads();
     const uint32_t lo = s_lo, cnt = s_cnt;
     for (uint32_t e = threadIdx.x; e < cnt; e += EP_THREADS) {
@@ -582,7 +602,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         contrib |= ok;
         const float al = ok ? alpha : 0.f;
         const float oma = 1.f - al;
-        const float ioma = __frcp_rn(oma);
+        const float ioma = __fdividef(1.f, oma);  // no decision depends on T here
         const float Ti = T[k] * ioma;
         const float w = al * Ti;
         v[6] += w * gr[k];

@@ -164,7 +164,8 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaMallocHost(&kvis_host_pinned, (uint64_t)cfg.max_batch * words * sizeof(uint32_t)));
   TGS_CUDA(cudaMallocHost(&r_host_pinned, words * sizeof(uint32_t)));
   dalloc(rl_dev, 3ull * max_items);
-  TGS_CUDA(cudaMallocHost(&rl_host, 3ull * max_items * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&rl_host, RL_RING * 3ull * max_items * sizeof(uint32_t)));
+  for (auto& e : rl_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   const uint64_t pix = (uint64_t)cfg.max_width * cfg.max_height;
   cams.resize(cfg.max_batch);
   dalloc(abort_dev, 2);
@@ -294,6 +295,8 @@ void Table::destroy() {
   for (void* p : hst)
     if (p) cudaFreeHost(p);
   for (auto& e : slot_free_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : rl_ev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap, ev_tgt_ready,
                         ev_tgt_used[0], ev_tgt_used[1]})
@@ -591,16 +594,23 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
       tgt = dst;
     }
   }
+  // the render list goes up from a ring of pinned staging slots: a slot is
+  // rewritten only after the copy that last read it has run
+  const uint32_t rs = (uint32_t)(rl_seq++ % RL_RING);
+  if (rl_ev_used[rs]) TGS_CUDA(cudaEventSynchronize(rl_ev[rs]));
+  uint32_t* rlh = rl_host + (uint64_t)rs * 3 * max_items;
   for (uint32_t j = 0; j < n_items; ++j) {
     uint32_t b = p.render_blocks[j];
-    rl_host[j] = p.render_slots[j];
-    rl_host[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - (uint64_t)b * B);
-    rl_host[2ull * max_items + j] = b;
+    rlh[j] = p.render_slots[j];
+    rlh[max_items + j] = (uint32_t)std::min<uint64_t>(B, N - (uint64_t)b * B);
+    rlh[2ull * max_items + j] = b;
   }
   if (n_items) {
     for (int q = 0; q < 3; ++q)
-      TGS_CUDA(cudaMemcpyAsync(rl_dev + (uint64_t)q * max_items, rl_host + (uint64_t)q * max_items,
+      TGS_CUDA(cudaMemcpyAsync(rl_dev + (uint64_t)q * max_items, rlh + (uint64_t)q * max_items,
                                n_items * sizeof(uint32_t), cudaMemcpyHostToDevice, comp));
+    TGS_CUDA(cudaEventRecord(rl_ev[rs], comp));
+    rl_ev_used[rs] = 1;
   }
   RenderList rl = render_list(n_items);
   const uint64_t V = rl.capacity();

@@ -60,7 +60,11 @@ struct Table {
   uint32_t* kvis_host_pinned = nullptr;  // pinned, max_batch x words
   uint32_t* r_host_pinned = nullptr;     // pinned, words
   uint32_t* rl_dev = nullptr;      // item_slot | item_count | item_block
-  uint32_t* rl_host = nullptr;     // pinned
+  static constexpr uint32_t RL_RING = 4;
+  uint32_t* rl_host = nullptr;     // pinned, RL_RING staging slots of 3 x max_items
+  cudaEvent_t rl_ev[RL_RING] = {};  // after the copy from each slot
+  int rl_ev_used[RL_RING] = {};
+  uint64_t rl_seq = 0;
   std::vector<CamState> cams;
   float* images = nullptr;
   float* dl_dimg = nullptr;
