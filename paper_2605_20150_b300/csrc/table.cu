@@ -34,9 +34,13 @@ static double camera_distance(const tgs_camera& a, const tgs_camera& b) {
 
 namespace {
 
+// Device allocations of the table start zeroed: no state is ever read from
+// memory a previous owner left behind.
 template <class T>
 void dalloc(T*& p, uint64_t count) {
-  TGS_CUDA(cudaMalloc((void**)&p, (count > 0 ? count : 1) * sizeof(T)));
+  const uint64_t bytes = (count > 0 ? count : 1) * sizeof(T);
+  TGS_CUDA(cudaMalloc((void**)&p, bytes));
+  TGS_CUDA(cudaMemset(p, 0, bytes));
 }
 
 void dfree(void* p) {
@@ -266,6 +270,7 @@ void Table::set_params(const float* params) {
   TGS_CUDA(cudaMemcpy(ages, a.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
   TGS_CUDA(cudaMemset(block_step, 0, K * sizeof(uint32_t)));
   TGS_CUDA(cudaMemset(dirty_dev, 0, n_slots));
+  TGS_CUDA(cudaMemset(abort_dev, 0, 2 * sizeof(uint32_t)));
   for (uint32_t* b : {r_bits, r_next_bits, acc_bits, acc_next_bits}) TGS_CUDA(cudaMemset(b, 0, words * sizeof(uint32_t)));
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
