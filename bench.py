@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="street100m", choices=["aerial2m", "street100m"])
+    ap.add_argument("--workload", default="street100m", choices=["aerial2m", "street100m", "city"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--cams", type=int, default=None)
     ap.add_argument("--cache-gb", type=float, default=24.0, help="HBM working-set cache cap (street workload)")
@@ -489,11 +489,33 @@ def cpu_baseline_street(res):
 
 # FP32 lane instructions per evaluated (pixel, splat) pair of the method's
 # compositing (an FMA counts once; exp, the comparisons and the reciprocal
-# count once each): forward 22, backward 50 (the counts are derived term by
+# count once each): forward 22, backward 40 (the counts are derived term by
 # term in the design notes).
-RASTER_INSTR = {"raster_fwd": 22.0, "raster_bwd": 50.0}
+RASTER_INSTR = {"raster_fwd": 22.0, "raster_bwd": 40.0}
 # FP32 lane peak: 148 SMs x 128 FP32 lanes x 2.032 GHz
 FP32_LANE_PEAK = 148 * 128 * 2.032e9
+
+
+def profiled_traffic(stage):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    if stage != "raster_bwd":
+        return None
+    path = os.path.join(ROOT, "profiles", "raster_adam_street100m_cache2gb.md")
+    src = os.path.join(ROOT, "paper_2605_20150_b300", "csrc", "raster.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- traffic_bytes_per_launch:"):
+            vals["t"] = int(line.split(":")[1])
+        if line.startswith("- source_sha256("):
+            vals["sha"] = line.split(":")[1].strip()
+    return vals.get("t") if vals.get("sha") == sha else None
 
 
 def roofline(res, steps):
@@ -512,7 +534,7 @@ def roofline(res, steps):
         evals = float(res["rec"]["n_last"].astype(np.float64).sum())
         ach = evals * RASTER_INSTR[name] / (ms_per * 1e-3)
         out.update(bound="alu", achieved=round(ach / 1e12, 3), peak=round(FP32_LANE_PEAK / 1e12, 2),
-                   unit="T FP32 lane-instr/s", frac=round(ach / FP32_LANE_PEAK, 4), traffic=None,
+                   unit="T FP32 lane-instr/s", frac=round(ach / FP32_LANE_PEAK, 4), traffic=profiled_traffic(name),
                    evals_per_launch=evals, instr_per_eval=RASTER_INSTR[name],
                    peak_source="derived: 148 SMs x 128 FP32 lanes x 2.032 GHz")
     elif name == "adam":
@@ -637,6 +659,122 @@ def reference_aerial(args):
     return _reference_line(args, v, cb, config)
 
 
+def host_mem_available():
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+
+
+def run_city(args, rank, world, local):
+    """The mixed city configuration (config 4's shape): street grid with roof
+    detail over 16 km^2, SH-rest and Adam moments BF16 in pinned host memory,
+    2,000 cameras at 1920x1080 (an aerial lawnmower pass at 150 m, pitch 45
+    degrees, then two street drives), batch 4, exact next-batch prefetch.  The
+    Gaussian count is the largest the host memory holds (the full 1.1B needs
+    about 420 GB of BF16 records); the HBM cache is capped in proportion (160 GB
+    for 1.1B, so about 38% of the scene).  Timed: one window of the aerial pass
+    and one of the street drives."""
+    import torch
+    import paper_2605_20150_b300 as tgs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    avail = host_mem_available() // max(world, 1)
+    n = args.n or int(min(1.1e9, 0.7 * avail / (236 + 382)))
+    nc = args.cams or 2000
+    J = 4
+    t0 = time.perf_counter()
+    host = np.empty((n, 59), np.float32)
+    chunk = 1 << 25
+    gt_dev = scenes.street_scene(n, device=dev, roof_frac=0.3, chunk=1 << 24, out_host=host)[1]
+    cams = scenes.city_cameras(nc)
+    W, H = cams[0]["width"], cams[0]["height"]
+    cache = int(160e9 * n / 1.1e9 // (4096 * 382))
+    base = dict(block_size=4096, max_batch=J, max_width=W, max_height=H, cache_blocks=cache, spare_slots=1024,
+                moments_policy=0, loss=0, host_bf16=1, stochastic_round=1, prefetch_mode=1, max_render_blocks=6144)
+    tb = tgs.TideTable(host, **base)
+    nb = args.warmup + args.steps
+    half = (nb + 1) // 2
+    windows = [list(range(0, J * half)), list(range(nc // 2, nc // 2 + J * (nb - half)))]
+    sel = [i for w in windows for i in w]
+    targets = torch.empty(len(sel), H, W, 3, device=dev)
+    for k, i in enumerate(sel):
+        tb.render(cams[i], targets[k])
+    torch.cuda.synchronize()
+    for a in range(0, n, chunk):
+        rows = torch.from_numpy(host[a:a + chunk]).to(dev)
+        scenes.t_perturb_(rows, 2004, a, mean_std=0.02 * gt_dev)
+        host[a:a + chunk] = rows.cpu().numpy()
+    tb.set_params(host)
+    t_setup = time.perf_counter() - t0
+    batches = [sel[k:k + J] for k in range(0, len(sel), J)]
+    tix = {i: k for k, i in enumerate(sel)}
+    s = torch.cuda.current_stream()
+
+    def one(b):
+        ids = batches[b]
+        nxt = batches[b + 1] if b + 1 < len(batches) else None
+        k0 = tix[ids[0]]
+        tb.step([cams[i] for i in ids], targets[k0:k0 + J], next_cams=[cams[i] for i in nxt] if nxt else None,
+                want_loss=False)
+
+    for b in range(args.warmup):
+        one(b)
+    tb.sync()
+    st0 = tb.stats()
+    tb.stage_timing(True)
+    tb.stage_ms(reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed:city")
+    e0.record(s)
+    for b in range(args.warmup, nb):
+        one(b)
+    e1.record(s)
+    torch.cuda.nvtx.range_pop()
+    tb.sync()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    stages = tb.stage_ms(reset=True)
+    tb.stage_timing(False)
+    st = tb.stats()
+    rec = tb.camera_record(0, W, H)
+    d = {k: st[k] - st0[k] for k in ("bytes_h2d", "bytes_d2h", "blocks_in", "blocks_out", "writebacks",
+                                     "readmissions", "stall_ms", "h2d_ms", "d2h_ms", "kernel_launches",
+                                     "demand_blocks", "demand_hits")}
+    peak = link_peak(torch)
+    link = {"peak_gbs": peak, "bytes_h2d_per_step": d["bytes_h2d"] / args.steps,
+            "bytes_d2h_per_step": d["bytes_d2h"] / args.steps,
+            "h2d_gbs_while_copying": round(d["bytes_h2d"] / max(d["h2d_ms"], 1e-9) / 1e6, 2),
+            "d2h_gbs_while_copying": round(d["bytes_d2h"] / max(d["d2h_ms"], 1e-9) / 1e6, 2),
+            "stall_ms_per_step": round(d["stall_ms"] / args.steps, 4),
+            "blocks_in_per_step": d["blocks_in"] / args.steps, "blocks_out_per_step": d["blocks_out"] / args.steps,
+            "writebacks": d["writebacks"], "readmissions": d["readmissions"],
+            "demand_hit_rate": round(d["demand_hits"] / max(d["demand_blocks"], 1), 5)}
+    # end to end: host targets of the first batches, losses read back
+    host_t = torch.empty(J * 4, H, W, 3, dtype=torch.float32, pin_memory=True)
+    host_t.copy_(targets[:J * 4].cpu())
+    hn = host_t.numpy()
+    n_e2e = 4
+    tb.losses()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for b in range(n_e2e):
+        ids = batches[b]
+        tb.step([cams[i] for i in ids], hn[J * b:J * b + J], next_cams=[cams[i] for i in batches[b + 1]],
+                want_loss=False)
+    assert len(tb.losses()) == n_e2e
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
+    return dict(ms=ms, stages=stages, stats=st, launches=d["kernel_launches"], clocks=clocks, rec=rec, table=tb,
+                e2e_ms=e2e_ms, bytes_in=J * H * W * 3 * 4, link=link, n=n, nc=nc, W=W, H=H, cache_blocks=cache,
+                setup_s=round(t_setup, 1), bf16=True, host_avail_gb=round(avail / 1e9, 1))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -650,7 +788,11 @@ def main():
         print(json.dumps(line))
         return
     street = args.workload == "street100m"
-    res = run_street(args, rank, world, local) if street else run_ours(args, rank, world, local)
+    city = args.workload == "city"
+    if city:
+        res = run_city(args, rank, world, local)
+    else:
+        res = run_street(args, rank, world, local) if street else run_ours(args, rank, world, local)
     ms_step = res["ms"] / args.steps
     value = world * 1e3 / ms_step
     if street:
@@ -661,6 +803,13 @@ def main():
                   "prefetch": "learned (MLP on the last 8 poses), exact culling for the actual batch",
                   "parallelism": f"replicas{world}", "l2": "per-step state > 126 MB L2, no flush",
                   "setup_s": res["setup_s"]}
+    elif city:
+        config = {"workload": f"city-{res['n'] / 1e6:.0f}M-1920x1080-batch4-outofcore-bf16",
+                  "n_gaussians": res["n"], "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": 4,
+                  "cameras": res["nc"], "cache_blocks": res["cache_blocks"],
+                  "scale": "largest N the host memory holds; cache capped at 160 GB x N / 1.1B",
+                  "host_available_gb": res["host_avail_gb"], "prefetch": "exact next batch",
+                  "parallelism": f"replicas{world}", "setup_s": res["setup_s"]}
     else:
         config = {"workload": "aerial-2M-1080p-resident-fp32", "n_gaussians": args.n or 2_000_000,
                   "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
@@ -678,13 +827,15 @@ def main():
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["stages"].items()},
         "visible": res["stats"]["last_visible"], "pairs": res["stats"]["last_pairs"],
     }
+    if city:
+        line["link"] = res["link"]
     if street:
         line["link"] = res["link"]
         line["forms"] = res["forms"]
         line["psnr_gap_db"] = res["psnr_gap_db"]
         line["vs_fp32_reactive"] = round(value / max(res["forms"]["fp32_reactive"]["iters_per_s"], 1e-9), 4)
         line["drive_b"] = res["drive_b"]
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not city:
         line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()
     if rank == 0:

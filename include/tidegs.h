@@ -67,7 +67,9 @@ typedef struct tgs_config {
   uint32_t prefetch_mode;  /* 0: reactive -- batch t's working set is selected and
                               streamed at step t (copies exposed);
                               1: exact next batch (Sec. 3.4-3.5) -- batch t+1's delta is
-                              selected and streamed while batch t computes */
+                              selected and streamed while batch t computes;
+                              2: learned (tgs_set_predictor); 3: exact lookahead over a
+                              schedule (tgs_set_schedule) */
   uint32_t overlap;        /* 1: copies on dedicated streams overlap compute (Sec. 3.4);
                               0: copies serialised with compute */
   uint64_t cache_blocks;   /* C, resident-set capacity in blocks; 0 = all blocks */
@@ -81,7 +83,9 @@ typedef struct tgs_config {
   float lr, beta1, beta2, eps; /* Adam, one learning rate for all 59 columns */
   float cull_margin_px;    /* Level-1 side-plane margin in pixels */
   float bg[3];             /* background colour */
-  uint32_t loss;           /* 0: L1 mean, 1: L2 mean (photometric loss f_i, App. A.1) */
+  uint32_t loss;           /* photometric loss f_i (App. A.1): 0 L1 mean, 1 L2 mean,
+                              2 the 3DGS recipe (1 - 0.2) L1 + 0.2 (1 - SSIM), SSIM over an
+                              11 x 11 Gaussian window (sigma 1.5), zero padding */
   uint32_t host_bf16;      /* 1: the 45 SH-rest coefficients and both Adam moments are
                               BF16 in the host tier and the cache (382 instead of 708
                               bytes per Gaussian; not in the paper); projection, blending
@@ -94,6 +98,18 @@ typedef struct tgs_config {
                               completed on the device without the excess, its step's update
                               is skipped, and the capacity grows once the host sees the
                               count (tgs_stats.pair_overflows / dropped_steps). */
+  uint64_t max_render_blocks; /* most blocks one batch renders (the per-camera buffers scale
+                              with it); 0 = cache_blocks.  A batch with more visible resident
+                              blocks is a TGS_ERR_CAPACITY error. */
+  /* Learning-rate schedule (Sec. 4 trains with "the 3DGS learning-rate
+   * schedule"): lr_schedule 0 = `lr` for all 59 columns; 1 = one rate per
+   * group (means, log-scales, quaternion, opacity, SH DC, SH rest) from
+   * lr_groups, the means' rate decaying log-linearly to lr_means_final over
+   * lr_decay_steps training steps (then constant). */
+  uint32_t lr_schedule;
+  float lr_groups[6];
+  float lr_means_final;
+  uint32_t lr_decay_steps;
 } tgs_config;
 
 void tgs_default_config(tgs_config* cfg);
@@ -110,6 +126,19 @@ typedef struct tgs_table tgs_table;
 tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_host, tgs_table** out);
 
 void tgs_destroy(tgs_table* t);
+
+/* Checkpoint and resume of the training state (Sec. 3.5's consistency
+ * barrier: every dirty resident block is written back first).  The file holds
+ * the Morton order, the host tier (parameters and Adam moments of every
+ * block), the per-block Adam step counters, the residency ages and the block
+ * bounds.  tgs_resume creates a table from it with an empty HBM cache (blocks
+ * stream in as they are needed); cfg must give the checkpoint's block_size
+ * and host_bf16, the other fields (cache size, prefetch, image limits) may
+ * differ.  path: host string, the file is created or replaced.
+ * Errors: TGS_ERR_INVALID (unreadable, truncated or mismatching file),
+ * TGS_ERR_OOM, TGS_ERR_CUDA. */
+tgs_status tgs_checkpoint(tgs_table* t, const char* path);
+tgs_status tgs_resume(const tgs_config* cfg, const char* path, tgs_table** out);
 
 /* One training step on a camera batch (Sec. 3.2 stages 1-4, Algorithm 1):
  * culls the batch's blocks, makes its working set resident (streaming only the
@@ -153,6 +182,14 @@ tgs_status tgs_losses(tgs_table* t, float* out_host, uint64_t max_count, uint64_
 /* Changes prefetch_mode (0 reactive, 1 exact next batch, 2 learned) between
  * steps; a pending prefetch is kept and used if it matches the next batch. */
 tgs_status tgs_set_prefetch_mode(tgs_table* t, uint32_t mode);
+
+/* Known trajectory for the exact lookahead prefetch (prefetch_mode 3; not in
+ * the paper, the upper bound the learned form is measured against): each step
+ * moves a cursor past its batch and, while the batch computes, selects
+ * (Algorithm 1, no access update) and streams the Level-1 visible blocks of
+ * the next `horizon` scheduled cameras.  cams: host, n cameras in step order
+ * (copied); horizon: 1..8.  Errors: TGS_ERR_INVALID. */
+tgs_status tgs_set_schedule(tgs_table* t, const tgs_camera* cams, uint64_t n, uint32_t horizon);
 
 /* Waits for all queued work of the table. */
 tgs_status tgs_sync(tgs_table* t);

@@ -229,6 +229,10 @@ def preprocess_bwd(P, cam_arr, S, G2):
 
 
 def loss(img, target, kind=0):
+    """kind 0: L1 mean, 1: L2 mean, 2: (1 - 0.2) L1 + 0.2 (1 - SSIM) (oracle/ssim.py)."""
+    if kind == 2:
+        from . import ssim
+        return ssim.loss(img, target), ssim.loss_grad(img, target)
     img = _f64(img)
     g = np.zeros_like(img)
     f = lib().orc_loss
@@ -237,11 +241,36 @@ def loss(img, target, kind=0):
     return val, g
 
 
+# parameter groups of the 59 columns: means, log-scales, quaternion, opacity,
+# SH DC, SH rest
+LR_GROUP_COLUMNS = ((0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 59))
+
+
+def group_lr(lr_groups):
+    """Per-column learning rates (59) from the six group rates."""
+    out = np.zeros(59, np.float64)
+    for (a, b), v in zip(LR_GROUP_COLUMNS, lr_groups):
+        out[a:b] = v
+    return out
+
+
+def lr_schedule_groups(lr_groups, lr_means_final, decay_steps, step):
+    """3DGS schedule: the means' rate decays log-linearly from its initial to
+    its final value over decay_steps (constant afterwards); the other groups
+    keep their rates.  step counts completed training steps."""
+    t = min(max(step, 0), decay_steps) / max(decay_steps, 1)
+    g = list(lr_groups)
+    g[0] = float(np.exp(np.log(lr_groups[0]) * (1.0 - t) + np.log(lr_means_final) * t))
+    return g
+
+
 def adam(P, Gr, M1, M2, mask, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-15):
-    """In place on float64 P, M1, M2 (n x 59); mask (n,) uint8; step (n,) int64."""
+    """In place on float64 P, M1, M2 (n x 59); mask (n,) uint8; step (n,)
+    int64; lr: one rate, or one per column (59)."""
+    lrv = np.ascontiguousarray(np.broadcast_to(np.asarray(lr, np.float64), (59,)), np.float64)
     lib().orc_adam(I64(P.shape[0]), _p(P), _p(_f64(Gr)), _p(M1), _p(M2),
                    _p(np.ascontiguousarray(mask, np.uint8)), _p(np.ascontiguousarray(step, np.int64)),
-                   ctypes.c_double(lr), ctypes.c_double(b1), ctypes.c_double(b2), ctypes.c_double(eps))
+                   _p(lrv), ctypes.c_double(b1), ctypes.c_double(b2), ctypes.c_double(eps))
 
 
 def sh_basis(dirs):

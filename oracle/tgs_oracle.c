@@ -996,7 +996,8 @@ double orc_loss(int64_t n, const double* img, const double* target, int loss, do
 /* Rows with mask 0 are left untouched.  Pinned by the one-step closed form. */
 /* ------------------------------------------------------------------------ */
 void orc_adam(int64_t n, double* P, const double* Gr, double* M1, double* M2, const uint8_t* mask,
-              const int64_t* step, double lr, double b1, double b2, double eps) {
+              const int64_t* step, const double* lr, double b1, double b2, double eps) {
+  /* lr: one learning rate per parameter column (59) */
   for (int64_t i = 0; i < n; ++i) {
     if (!mask[i]) continue;
     double c1 = 1.0 - pow(b1, (double)step[i]);
@@ -1006,7 +1007,7 @@ void orc_adam(int64_t n, double* P, const double* Gr, double* M1, double* M2, co
       double g = Gr[e];
       M1[e] = b1 * M1[e] + (1.0 - b1) * g;
       M2[e] = b2 * M2[e] + (1.0 - b2) * g * g;
-      P[e] -= lr * (M1[e] / c1) / (sqrt(M2[e] / c2) + eps);
+      P[e] -= lr[j] * (M1[e] / c1) / (sqrt(M2[e] / c2) + eps);
     }
   }
 }

@@ -41,7 +41,9 @@ class tgs_config(ctypes.Structure):
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("cull_margin_px", ctypes.c_float), ("bg", ctypes.c_float * 3), ("loss", ctypes.c_uint32),
                 ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32),
-                ("pair_capacity", ctypes.c_uint64)]
+                ("pair_capacity", ctypes.c_uint64), ("max_render_blocks", ctypes.c_uint64),
+                ("lr_schedule", ctypes.c_uint32), ("lr_groups", ctypes.c_float * 6), ("lr_means_final", ctypes.c_float),
+                ("lr_decay_steps", ctypes.c_uint32)]
 
 
 class tgs_stats(ctypes.Structure):
@@ -67,6 +69,9 @@ _SIGS = {
     "tgs_render": (ctypes.c_int32, [_VP, ctypes.POINTER(tgs_camera), _VP, _VP]),
     "tgs_sync": (ctypes.c_int32, [_VP]),
     "tgs_losses": (ctypes.c_int32, [_VP, _VP, ctypes.c_uint64, _VP]),
+    "tgs_checkpoint": (ctypes.c_int32, [_VP, ctypes.c_char_p]),
+    "tgs_set_schedule": (ctypes.c_int32, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32]),
+    "tgs_resume": (ctypes.c_int32, [ctypes.POINTER(tgs_config), ctypes.c_char_p, ctypes.POINTER(_VP)]),
     "tgs_set_prefetch_mode": (ctypes.c_int32, [_VP, _U32]),
     "tgs_get_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_set_params": (ctypes.c_int32, [_VP, _VP]),
@@ -168,6 +173,9 @@ def default_config(**kw) -> tgs_config:
         if k == "bg":
             for i in range(3):
                 c.bg[i] = v[i]
+        elif k == "lr_groups":
+            for i in range(6):
+                c.lr_groups[i] = v[i]
         elif k == "lam":
             c.lambda_ = v
         else:
@@ -178,17 +186,28 @@ def default_config(**kw) -> tgs_config:
 class TideTable:
     """A block-virtualised table of N Gaussians (tgs_create ... tgs_destroy)."""
 
-    def __init__(self, params: np.ndarray, **cfg):
-        params = np.ascontiguousarray(params, np.float32)
-        assert params.ndim == 2 and params.shape[1] == D
-        self.n = params.shape[0]
+    def __init__(self, params: np.ndarray, _resume=None, **cfg):
         self.cfg = default_config(**cfg)
         h = ctypes.c_void_p()
-        _check(load().tgs_create(ctypes.byref(self.cfg), self.n, _ptr(params), ctypes.byref(h)))
+        if _resume is not None:
+            _check(load().tgs_resume(ctypes.byref(self.cfg), str(_resume).encode(), ctypes.byref(h)))
+        else:
+            params = np.ascontiguousarray(params, np.float32)
+            assert params.ndim == 2 and params.shape[1] == D
+            _check(load().tgs_create(ctypes.byref(self.cfg), params.shape[0], _ptr(params), ctypes.byref(h)))
         self.h = h
         n, k, s = _U64(), _U64(), _U64()
         _check(load().tgs_get_sizes(self.h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(s)))
-        self.K, self.slots = k.value, s.value
+        self.n, self.K, self.slots = n.value, k.value, s.value
+
+    @classmethod
+    def resume(cls, path, **cfg):
+        """A table from a checkpoint file (tgs_resume)."""
+        return cls(None, _resume=path, **cfg)
+
+    def checkpoint(self, path):
+        """Writes the training state to a file (tgs_checkpoint)."""
+        _check(load().tgs_checkpoint(self.h, str(path).encode()))
 
     def close(self):
         if getattr(self, "h", None):
@@ -228,6 +247,11 @@ class TideTable:
         n = _U64()
         _check(load().tgs_losses(self.h, _ptr(out), max_count, ctypes.byref(n)))
         return out[:n.value].copy()
+
+    def set_schedule(self, cams, horizon=2):
+        """Known trajectory for the exact lookahead prefetch (mode 3)."""
+        ca = camera_array(cams)
+        _check(load().tgs_set_schedule(self.h, ca, len(cams), horizon))
 
     def set_prefetch_mode(self, mode):
         _check(load().tgs_set_prefetch_mode(self.h, mode))

@@ -119,6 +119,14 @@ void tgs_default_config(tgs_config* c) {
   c->host_bf16 = 0;
   c->stochastic_round = 1;
   c->seed = 1234;
+  // 3DGS rates: means 1.6e-4 -> 1.6e-6 over 30k steps (scale by the scene
+  // extent), log-scales 5e-3, rotation 1e-3, opacity 5e-2, SH DC 2.5e-3,
+  // SH rest 2.5e-3 / 20
+  c->lr_schedule = 0;
+  const float g[6] = {1.6e-4f, 5e-3f, 1e-3f, 5e-2f, 2.5e-3f, 1.25e-4f};
+  for (int i = 0; i < 6; ++i) c->lr_groups[i] = g[i];
+  c->lr_means_final = 1.6e-6f;
+  c->lr_decay_steps = 30000;
 }
 
 tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_host, tgs_table** out) {
@@ -128,6 +136,29 @@ tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_hos
     tgs_table* t = new tgs_table();
     try {
       t->t.create(*cfg, n, params_host);
+    } catch (...) {
+      t->t.destroy();
+      delete t;
+      throw;
+    }
+    *out = t;
+  });
+}
+
+tgs_status tgs_checkpoint(tgs_table* t, const char* path) {
+  return guard([&] {
+    TGS_CHECK(t && path, TGS_ERR_INVALID, "tgs_checkpoint: null argument");
+    t->t.save(path);
+  });
+}
+
+tgs_status tgs_resume(const tgs_config* cfg, const char* path, tgs_table** out) {
+  return guard([&] {
+    TGS_CHECK(cfg && path && out, TGS_ERR_INVALID, "tgs_resume: null argument");
+    *out = nullptr;
+    tgs_table* t = new tgs_table();
+    try {
+      t->t.resume(*cfg, path);
     } catch (...) {
       t->t.destroy();
       delete t;
@@ -162,7 +193,7 @@ tgs_status tgs_render(tgs_table* t, const tgs_camera* cam, float* image_dev, voi
 
 tgs_status tgs_set_prefetch_mode(tgs_table* t, uint32_t mode) {
   return guard([&] {
-    TGS_CHECK(t && mode <= 2, TGS_ERR_INVALID, "tgs_set_prefetch_mode: bad argument");
+    TGS_CHECK(t && mode <= 3, TGS_ERR_INVALID, "tgs_set_prefetch_mode: bad argument");
     t->t.cfg.prefetch_mode = mode;
   });
 }
@@ -171,6 +202,16 @@ tgs_status tgs_losses(tgs_table* t, float* out_host, uint64_t max_count, uint64_
   return guard([&] {
     TGS_CHECK(t && out_host && count, TGS_ERR_INVALID, "tgs_losses: null argument");
     *count = t->t.losses(out_host, max_count);
+  });
+}
+
+tgs_status tgs_set_schedule(tgs_table* t, const tgs_camera* cams, uint64_t n, uint32_t horizon) {
+  return guard([&] {
+    TGS_CHECK(t && (cams || n == 0), TGS_ERR_INVALID, "tgs_set_schedule: null argument");
+    TGS_CHECK(horizon >= 1 && horizon <= Table::MAX_LOOKAHEAD, TGS_ERR_INVALID, "tgs_set_schedule: horizon out of [1, 8]");
+    t->t.schedule.assign(cams, cams + n);
+    t->t.sched_pos = 0;
+    t->t.sched_horizon = horizon;
   });
 }
 

@@ -486,10 +486,15 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
       const float4 bb = sp[j].b;
       const float cb = sp[j].c;
       act = false;
+      // the thread's pixels share their column: dx and A dx^2 once (the same
+      // correctly rounded operations as splat_power)
+      const float dx = __fsub_rn(fpx, a.x);
+      const float adxx = __fmul_rn(a.z, __fmul_rn(dx, dx));
 #pragma unroll
       for (int k = 0; k < R_PPT; ++k) {
-        float dx, dy;
-        const float power = splat_power(fpx, (float)(q.py0 + k), a.x, a.y, a.z, a.w, bb.x, dx, dy);
+        const float dy = __fsub_rn((float)(q.py0 + k), a.y);
+        const float qf = __fadd_rn(adxx, __fmul_rn(bb.x, __fmul_rn(dy, dy)));
+        const float power = __fsub_rn(__fmul_rn(-0.5f, qf), __fmul_rn(a.w, __fmul_rn(dx, dy)));
         float G;
         const float alpha = splat_alpha(bb.y, power, G);
         const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
@@ -548,7 +553,9 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
   Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
   const float fpx = (float)q.px;
-  float T[R_PPT], gr[R_PPT], gg[R_PPT], gb[R_PPT], S0[R_PPT], S1[R_PPT], S2[R_PPT], tfb[R_PPT];
+  // Qs = sum_c dL/dC_c S_c, S_c the colour composited behind the current
+  // splat (only this combination enters dL/dalpha)
+  float T[R_PPT], gr[R_PPT], gg[R_PPT], gb[R_PPT], Qs[R_PPT], tfb[R_PPT];
   int last[R_PPT];
   int mylast = 0;
 #pragma unroll
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
     T[k] = 1.f;
     last[k] = 0;
     gr[k] = gg[k] = gb[k] = 0.f;
-    S0[k] = S1[k] = S2[k] = 0.f;
+    Qs[k] = 0.f;
     if (q.px < W && py < H) {
       const uint64_t pix = (uint64_t)py * W + q.px;
       T[k] = t_final[pix];
@@ -590,12 +597,21 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       const float4 a = sp[j].a;
       const float4 bb = sp[j].b;
       const float cb = sp[j].c;
+      // v: sums over the warp's pixels of dpw dx, dpw dy, dpw dx^2, dpw dx dy,
+      // dpw dy^2 (dpw = dL/dpower; the conic and constant factors are applied
+      // after the reduction), dL/dopacity-activation, dL/d(r, g, b)
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
+      const float dx = __fsub_rn(fpx, a.x);
+      const float dxx = __fmul_rn(dx, dx);
+      const float adxx = __fmul_rn(a.z, dxx);
 #pragma unroll
       for (int k = 0; k < R_PPT; ++k) {
-        float dx, dy;
-        const float power = splat_power(fpx, (float)(q.py0 + k), a.x, a.y, a.z, a.w, bb.x, dx, dy);
+        const float dy = __fsub_rn((float)(q.py0 + k), a.y);
+        const float dyy = __fmul_rn(dy, dy);
+        const float dxy = __fmul_rn(dx, dy);
+        const float qf = __fadd_rn(adxx, __fmul_rn(bb.x, dyy));
+        const float power = __fsub_rn(__fmul_rn(-0.5f, qf), __fmul_rn(a.w, dxy));
         float G;
         const float alpha = splat_alpha(bb.y, power, G);
         const bool ok = pos < last[k] && power <= 0.f && alpha >= ALPHA_MIN;
@@ -608,20 +624,18 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         v[6] += w * gr[k];
         v[7] += w * gg[k];
         v[8] += w * gb[k];
-        const float dal = Ti * (gr[k] * (bb.z - S0[k]) + gg[k] * (bb.w - S1[k]) + gb[k] * (cb - S2[k])) -
-                          tfb[k] * ioma;
-        S0[k] = al * bb.z + oma * S0[k];
-        S1[k] = al * bb.w + oma * S1[k];
-        S2[k] = al * cb + oma * S2[k];
+        const float pc = gr[k] * bb.z + gg[k] * bb.w + gb[k] * cb;
+        const float dal = Ti * (pc - Qs[k]) - tfb[k] * ioma;
+        Qs[k] = al * pc + oma * Qs[k];
         T[k] = Ti;
         const float dsel = (ok && __fmul_rn(bb.y, G) <= ALPHA_MAX) ? dal : 0.f;
         v[5] += G * dsel;
         const float dpw = al * dsel;
-        v[0] += dpw * (a.z * dx + a.w * dy);
-        v[1] += dpw * (a.w * dx + bb.x * dy);
-        v[2] += -0.5f * dpw * dx * dx;
-        v[3] += -dpw * dx * dy;
-        v[4] += -0.5f * dpw * dy * dy;
+        v[0] += dpw * dx;
+        v[1] += dpw * dy;
+        v[2] += dpw * dxx;
+        v[3] += dpw * dxy;
+        v[4] += dpw * dyy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
         float b4[4];
@@ -642,9 +656,18 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
         b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
         const float s8 = warp_sum(v[8]);
+        // d power / du = A dx + B dy, d power / dv = B dx + C dy: the lanes of
+        // sums 0 and 1 (lanes l and l ^ 4) swap their sums; conic gradients
+        // carry the factors -1/2, -1, -1/2
+        const float other = __shfl_xor_sync(0xffffffffu, b1, 4);
+        float fin = b1;
+        if (qsel == 0) fin = a.z * b1 + a.w * other;
+        else if (qsel == 1) fin = a.w * other + bb.x * b1;
+        else if (qsel == 2 || qsel == 4) fin = -0.5f * b1;
+        else if (qsel == 3) fin = -b1;
         const uint32_t id = sp[j].id;
         if ((lane & 3) == 0) {
-          if (b1 != 0.f) atomicAdd(&g2[(uint64_t)qsel * V + id], b1);
+          if (fin != 0.f) atomicAdd(&g2[(uint64_t)qsel * V + id], fin);
         } else if (lane == 1 && s8 != 0.f) {
           atomicAdd(&g2[8ull * V + id], s8);
         }
@@ -897,7 +920,7 @@ constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
 template <bool BF>
 __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __restrict__ grad,
                                          const float2* __restrict__ bias, const uint32_t* __restrict__ block_step,
-                                         uint64_t V, float lr, float b1, float b2, float eps, unsigned item,
+                                         uint64_t V, const LrSet& lrs, float b1, float b2, float eps, unsigned item,
                                          unsigned lane, uint64_t i, int f0) {
   const uint32_t B = rl.B;
   const float2 bc = bias[item];
@@ -917,7 +940,7 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         float vf = b2 * v[o] + (1.f - b2) * gf * gf;
         m[o] = mf;
         v[o] = vf;
-        p[o] -= lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+        p[o] -= lrs.g[lr_group(f)] * (mf * ic1) / (sqrtf(vf * ic2) + eps);
       }
     }
   } else {
@@ -937,7 +960,7 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         float gf = grad[(uint64_t)f * V + i];
         float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
         float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
-        const float upd = lr * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+        const float upd = lrs.g[lr_group(f)] * (mf * ic1) / (sqrtf(vf * ic2) + eps);
         const uint64_t key = key0 + (uint64_t)f * 4;
         m[o] = to_bf16(mf, sr, key);
         v[o] = to_bf16(vf, sr, key + 1);
@@ -962,7 +985,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
                                                     const uint32_t* __restrict__ rows,
                                                     const uint32_t* __restrict__ nrows,
                                                     const float2* __restrict__ bias,
-                                                    const uint32_t* __restrict__ block_step, uint64_t V, float lr,
+                                                    const uint32_t* __restrict__ block_step, uint64_t V, LrSet lrs,
                                                     float b1, float b2, float eps,
                                                     const uint32_t* __restrict__ abort_flag) {
   if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
@@ -971,7 +994,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
   for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
     const uint32_t i = rows[t];
     const unsigned item = i / B, lane = i - item * B;
-    adam_row<BF>(rl, grad, bias, block_step, V, lr, b1, b2, eps, item, lane, i, f0);
+    adam_row<BF>(rl, grad, bias, block_step, V, lrs, b1, b2, eps, item, lane, i, f0);
   }
 }
 
@@ -1400,7 +1423,7 @@ void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, 
 }
 
 void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
-                      const float2* bias, const uint32_t* block_step, float lr, float b1, float b2, float eps,
+                      const float2* bias, const uint32_t* block_step, const LrSet& lr, float b1, float b2, float eps,
                       cudaStream_t s, const uint32_t* abort_flag) {
   if (rl.capacity() == 0) return;
   const dim3 grid(std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM), ADAM_GROUPS);

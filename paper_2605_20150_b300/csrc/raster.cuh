@@ -116,9 +116,18 @@ void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, 
 // moments in the pool are updated; `grad` is the local [59][rl.capacity()] array; step counters per
 // block id (already incremented for this step).  Nothing is updated while
 // *abort_flag (device, may be null) is set.
+// Learning rates of the six parameter groups (means, log-scales, quaternion,
+// opacity, SH DC, SH rest) for one step.
+struct LrSet {
+  float g[6];
+};
+__host__ __device__ inline int lr_group(int f) {
+  return f < 3 ? 0 : f < 6 ? 1 : f < 10 ? 2 : f < 11 ? 3 : f < 14 ? 4 : 5;
+}
+
 // bias: per item (1 / (1 - b1^step), 1 / (1 - b2^step)) from mark_touched_blocks.
 void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
-                      const float2* bias, const uint32_t* block_step, float lr, float b1, float b2, float eps,
+                      const float2* bias, const uint32_t* block_step, const LrSet& lr, float b1, float b2, float eps,
                       cudaStream_t s, const uint32_t* abort_flag = nullptr);
 
 // Per-item bookkeeping before Adam: for items with item_touched != 0,
@@ -132,6 +141,13 @@ void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uin
 
 // touched[j * B + l] |= (Gaussian l of item j had a non-empty tile rect in cs).
 void mark_visible_bytes(const RenderList& rl, const CamState& cs, uint8_t* touched, cudaStream_t s);
+
+// The 3DGS photometric loss with the D-SSIM term on J images (H x W x 3,
+// interleaved): adds the loss sum ((1 - 0.2) |x - y| + 0.2 (1 - SSIM) over
+// every value) to *loss_sum and writes dL/dimage of the mean into grad.
+// scratch: device, 3 x J x H x W x 3 floats.
+void photometric_loss_ssim(const float* img, const float* target, int J, int W, int H, float* grad, float* loss_sum,
+                           float* scratch, cudaStream_t s);
 
 // Masked Adam on block-layout arrays [ceil(n/B)][59][B]: per-block step
 // counters are incremented for blocks with a touched row, then touched rows

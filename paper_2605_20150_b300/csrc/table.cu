@@ -8,7 +8,9 @@
 // computes (Sec. 3.4 "Hierarchical asynchronous execution"); blocks that can
 // only go into slots freed by S- are copied after that write-back.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <thread>
 
 #include <cuda_bf16.h>
@@ -66,13 +68,14 @@ RenderList Table::render_list(uint32_t n_items) const {
   return rl;
 }
 
-void Table::create(const tgs_config& c, uint64_t n, const float* params) {
+void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FILE* ck) {
   cfg = c;
-  TGS_CHECK(n > 0 && params, TGS_ERR_INVALID, "tgs_create: n must be > 0 and params non-null");
+  TGS_CHECK(n > 0 && (params || ck), TGS_ERR_INVALID, "tgs_create: n must be > 0 and params non-null");
   TGS_CHECK(c.block_size >= 1 && c.block_size <= 65536, TGS_ERR_INVALID, "block_size out of range [1, 65536]");
   TGS_CHECK(c.max_batch >= 1 && c.max_width >= 1 && c.max_height >= 1, TGS_ERR_INVALID, "bad batch/image limits");
   TGS_CHECK(n < (1ull << 32), TGS_ERR_INVALID, "n must be below 2^32");
   TGS_CHECK(c.host_bf16 == 0 || c.block_size % 2 == 0, TGS_ERR_INVALID, "host_bf16 needs an even block_size");
+  TGS_CHECK(c.loss <= 2, TGS_ERR_INVALID, "loss must be 0 (L1), 1 (L2) or 2 (L1 + D-SSIM)");
   N = n;
   B = c.block_size;
   K = (N + B - 1) / B;
@@ -90,7 +93,9 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
     m_floats = (uint64_t)D * B;
   }
   rec_floats = p_floats + 2 * m_floats;
-  max_items = (uint32_t)C;
+  // render-list capacity (the per-camera buffers scale with it): the cache
+  // capacity unless a smaller bound on one batch's visible blocks is given
+  max_items = (uint32_t)(c.max_render_blocks && c.max_render_blocks < C ? c.max_render_blocks : C);
   V_cap = (uint64_t)max_items * B;
 
   // the control stream's short selection kernels are scheduled ahead of the
@@ -108,29 +113,38 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaEventCreate(&ev_stall_b));
   copy_timer.on = true;
 
-  // ---- Morton order on the device (Sec. 3.3): centres -> codes -> stable sort
-  {
-    float* means = nullptr;
-    uint32_t *codes = nullptr, *pm = nullptr;
-    void* scr = nullptr;
-    float* aabb = nullptr;
-    dalloc(means, 3 * N);
-    dalloc(codes, 2 * N);
-    dalloc(pm, 2 * N);
-    TGS_CUDA(cudaMalloc(&scr, radix_scratch_bytes(N)));
-    dalloc(aabb, 16);
-    TGS_CUDA(cudaMemcpy2DAsync(means, 3 * sizeof(float), params, D * sizeof(float), 3 * sizeof(float), N,
-                               cudaMemcpyHostToDevice, comp));
-    morton_order(means, N, pm, codes, codes + N, pm + N, scr, aabb, comp);
+  if (ck) {
+    // a checkpoint brings its own Morton order
     perm.resize(N);
-    TGS_CUDA(cudaMemcpyAsync(perm.data(), pm, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, comp));
-    TGS_CUDA(cudaStreamSynchronize(comp));
-    dfree(means); dfree(codes); dfree(pm); dfree(scr); dfree(aabb);
+    ck_read(ck, perm.data(), N * sizeof(uint32_t));
+  } else {
+    // ---- Morton order on the device (Sec. 3.3): centres -> codes -> stable sort
+    {
+      float* means = nullptr;
+      uint32_t *codes = nullptr, *pm = nullptr;
+      void* scr = nullptr;
+      float* aabb = nullptr;
+      dalloc(means, 3 * N);
+      dalloc(codes, 2 * N);
+      dalloc(pm, 2 * N);
+      TGS_CUDA(cudaMalloc(&scr, radix_scratch_bytes(N)));
+      dalloc(aabb, 16);
+      TGS_CUDA(cudaMemcpy2DAsync(means, 3 * sizeof(float), params, D * sizeof(float), 3 * sizeof(float), N,
+                                 cudaMemcpyHostToDevice, comp));
+      morton_order(means, N, pm, codes, codes + N, pm + N, scr, aabb, comp);
+      perm.resize(N);
+      TGS_CUDA(cudaMemcpyAsync(perm.data(), pm, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, comp));
+      TGS_CUDA(cudaStreamSynchronize(comp));
+      dfree(means); dfree(codes); dfree(pm); dfree(scr); dfree(aabb);
+    }
   }
 
   // ---- host tier: K block records [params | m | v], field-major inside
   TGS_CUDA(cudaHostAlloc((void**)&host, K * rec_floats * sizeof(float), cudaHostAllocPortable));
-  fill_host(params);
+  if (ck)
+    ck_read(ck, host, K * rec_floats * sizeof(float));
+  else
+    fill_host(params);
 
   // ---- device cache and state
   dalloc(pool, n_slots * rec_floats);
@@ -151,9 +165,11 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
     dalloc(*b, words);
     TGS_CUDA(cudaMemsetAsync(*b, 0, words * sizeof(uint32_t), comp));
   }
-  dalloc(kvis, (uint64_t)cfg.max_batch * words);
-  dalloc(planes_dev, cfg.max_batch);
-  TGS_CUDA(cudaMallocHost(&planes_host, cfg.max_batch * sizeof(Planes)));
+  // visibility rows: a batch, or the cameras of an exact lookahead
+  vis_rows = std::max<uint32_t>(cfg.max_batch, MAX_LOOKAHEAD);
+  dalloc(kvis, (uint64_t)vis_rows * words);
+  dalloc(planes_dev, vis_rows);
+  TGS_CUDA(cudaMallocHost(&planes_host, vis_rows * sizeof(Planes)));
   dalloc(rb.flag, K);
   dalloc(rb.pos, K);
   dalloc(rb.key, 2 * K);
@@ -165,7 +181,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaMalloc(&rb.scratch, residency_scratch_bytes(K)));
   dalloc(lists_dev, 3 * K + 16);
   TGS_CUDA(cudaMallocHost(&lists_host, (3 * K + 16) * sizeof(uint32_t)));
-  TGS_CUDA(cudaMallocHost(&kvis_host_pinned, (uint64_t)cfg.max_batch * words * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&kvis_host_pinned, (uint64_t)vis_rows * words * sizeof(uint32_t)));
   TGS_CUDA(cudaMallocHost(&r_host_pinned, words * sizeof(uint32_t)));
   dalloc(rl_dev, 3ull * max_items);
   TGS_CUDA(cudaMallocHost(&rl_host, RL_RING * 3ull * max_items * sizeof(uint32_t)));
@@ -185,6 +201,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   dalloc(images, cfg.max_batch * pix * 3);
   dalloc(dl_dimg, cfg.max_batch * pix * 3);
   dalloc(targets_buf, 2 * cfg.max_batch * pix * 3);  // double buffer for host targets
+  if (cfg.loss == 2) dalloc(ssim_buf, 3 * cfg.max_batch * pix * 3);
   TGS_CUDA(cudaMallocHost(&loss_ring, LOSS_RING * sizeof(float)));
   loss_norm.assign(LOSS_RING, 1.f);
   dalloc(touched, V_cap);
@@ -197,6 +214,19 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params) {
   TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
 
   init_spheres();
+  if (ck) {
+    // optimiser and residency state, then the bounds as the saved table had them
+    std::vector<uint32_t> u(K);
+    ck_read(ck, u.data(), K * sizeof(uint32_t));
+    TGS_CUDA(cudaMemcpy(block_step, u.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    ck_read(ck, u.data(), K * sizeof(uint32_t));
+    TGS_CUDA(cudaMemcpy(ages, u.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    std::vector<float4> sp(K);
+    ck_read(ck, sp.data(), K * sizeof(float4));
+    TGS_CUDA(cudaMemcpy(spheres, sp.data(), K * sizeof(float4), cudaMemcpyHostToDevice));
+    ck_read(ck, sp.data(), K * sizeof(float4));
+    TGS_CUDA(cudaMemcpy(spheres_snap, sp.data(), K * sizeof(float4), cudaMemcpyHostToDevice));
+  }
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
   dirty_host.assign(n_slots, 0);
@@ -292,7 +322,7 @@ void Table::destroy() {
   for (auto& cs : cams) cam_state_free(cs);
   void* dev[] = {pool, spheres, spheres_snap, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
                  kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
-                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, touched, item_touched, item_bias, rows_dev, grad_local,
+                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, ssim_buf, touched, item_touched, item_bias, rows_dev, grad_local,
                  loss_dev, abort_dev};
   for (void* p : dev) dfree(p);
   void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host,
@@ -365,6 +395,22 @@ void Table::prepare_enqueue_predicted(Prepared& out) {
   mlp_predict_near(*predictor, spheres, K, h, reach, pred_mask, pred_threshold, kvis, ctl);
   TGS_CUDA(cudaMemcpyAsync(kvis_union, kvis, words * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctl));
   select_enqueue(1, out, false);
+}
+
+// Exact lookahead: the Level-1 visible sets of the next `horizon` cameras of
+// the schedule replace the prediction (the upper bound the learned form is
+// compared with); no ages or access are updated.
+void Table::prepare_enqueue_lookahead(Prepared& out) {
+  const uint64_t first = sched_pos;
+  const uint32_t H = (uint32_t)std::min<uint64_t>(sched_horizon, schedule.size() - std::min(first, (uint64_t)schedule.size()));
+  out = Prepared();
+  if (H == 0) return;
+  out.predicted = true;
+  for (uint32_t j = 0; j < H; ++j) planes_host[j] = frustum_planes(schedule[first + j], cfg.cull_margin_px);
+  TGS_CUDA(cudaMemcpyAsync(planes_dev, planes_host, H * sizeof(Planes), cudaMemcpyHostToDevice, ctl));
+  TGS_CUDA(cudaStreamWaitEvent(ctl, ev_comp, 0));
+  cull_blocks(spheres, K, planes_dev, (int)H, kvis, kvis_union, ctl);
+  select_enqueue(H, out, false);
 }
 
 // Algorithm 1 on the visible sets in kvis (J rows); counts and sets are copied
@@ -570,7 +616,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
                     bool backward, float* image_out) {
   const uint32_t J = (uint32_t)p.cams.size();
   const uint32_t n_items = (uint32_t)p.render_blocks.size();
-  TGS_CHECK(n_items <= max_items, TGS_ERR_CAPACITY, "render list exceeds the cache capacity");
+  TGS_CHECK(n_items <= max_items, TGS_ERR_CAPACITY, "render list exceeds the render-list capacity");
   const int W = (int)p.cams[0].width, H = (int)p.cams[0].height;
   const uint64_t pix = (uint64_t)W * H;
   collect_stall();
@@ -640,7 +686,10 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     // the rows the chain rule stores and the optimiser updates
     touched_rows(rl, touched, rows_dev, rows_dev + V_cap_rows, comp);
     timer.begin(StageTimer::LOSS, comp);
-    photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
+    if (cfg.loss == 2)
+      photometric_loss_ssim(images, tgt, (int)J, W, H, dl_dimg, loss_dev, ssim_buf, comp);
+    else
+      photometric_loss(images, tgt, (uint64_t)J * pix * 3, (int)cfg.loss, dl_dimg, loss_dev, comp);
     if (tgt_buf >= 0) {
       TGS_CUDA(cudaEventRecord(ev_tgt_used[tgt_buf], comp));
       tgt_used[tgt_buf] = 1;
@@ -662,8 +711,8 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     }
     timer.begin(StageTimer::ADAM, comp);
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias);
-    adam_render_list(rl, grad_local, rows_dev, rows_dev + V_cap_rows, item_bias, block_step, cfg.lr, cfg.beta1,
-                     cfg.beta2, cfg.eps, comp, abort_dev);
+    adam_render_list(rl, grad_local, rows_dev, rows_dev + V_cap_rows, item_bias, block_step, step_lrs(),
+                     cfg.beta1, cfg.beta2, cfg.eps, comp, abort_dev);
     timer.end(StageTimer::ADAM, comp);
     // the next batch's cull (control stream) reads the bounds first
     TGS_CUDA(cudaStreamWaitEvent(comp, ev_ctl, 0));
@@ -711,12 +760,15 @@ void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint3
   }
   const bool prefetch = cfg.prefetch_mode == 1 && next && nJ >= 1;
   const bool learned = cfg.prefetch_mode == 2 && predictor != nullptr;
+  const bool lookahead = cfg.prefetch_mode == 3 && !schedule.empty();
+  if (lookahead) sched_pos += J;  // the schedule cursor moves past this batch
   // Algorithm 1 for batch t+1 runs on the control stream while batch t is
   // enqueued; it sees the bounds as of the start of step t
   if (prefetch) prepare_enqueue(next, nJ, nxt, false);
   if (learned) prepare_enqueue_predicted(nxt);
+  if (lookahead) prepare_enqueue_lookahead(nxt);
   compute(cur, targets_dev, targets_host, user, true, nullptr);
-  if (prefetch || learned) {
+  if (prefetch || learned || (lookahead && nxt.enqueued)) {
     prepare_finish(nxt);
     issue_early(nxt);
     issue_evictions_and_late(nxt);
@@ -756,6 +808,19 @@ uint64_t Table::losses(float* out, uint64_t max_count) {
   return n;
 }
 
+LrSet Table::step_lrs() const {
+  LrSet r;
+  if (!cfg.lr_schedule) {
+    for (float& x : r.g) x = cfg.lr;
+    return r;
+  }
+  for (int i = 0; i < 6; ++i) r.g[i] = cfg.lr_groups[i];
+  const double T = cfg.lr_decay_steps > 0 ? (double)cfg.lr_decay_steps : 1.0;
+  const double t = std::min<double>((double)stats.steps, T) / T;
+  r.g[0] = (float)std::exp(std::log((double)cfg.lr_groups[0]) * (1.0 - t) + std::log((double)cfg.lr_means_final) * t);
+  return r;
+}
+
 bool Table::check_overflow(bool wait) {
   bool any = false;
   uint64_t need = 0;
@@ -776,6 +841,81 @@ bool Table::check_overflow(bool wait) {
   }
   TGS_CUDA(cudaMemset(abort_dev, 0, 2 * sizeof(uint32_t)));
   return true;
+}
+
+// ---- checkpoint file: "TGSCKPT1", header (u64: n, B, K, rec_floats,
+// host_bf16, moments_policy, steps), Morton permutation (u32 x n), host tier
+// (K records), block step counters, ages (u32 x K each), bounds and the
+// snapshot bounds (float4 x K each).
+static const char kCkMagic[8] = {'T', 'G', 'S', 'C', 'K', 'P', 'T', '1'};
+
+void ck_read(std::FILE* f, void* dst, uint64_t bytes) {
+  char* d = static_cast<char*>(dst);
+  while (bytes) {
+    const size_t n = std::fread(d, 1, std::min<uint64_t>(bytes, 1ull << 28), f);
+    TGS_CHECK(n > 0, TGS_ERR_INVALID, "checkpoint file is truncated");
+    d += n;
+    bytes -= n;
+  }
+}
+
+static void ck_write(std::FILE* f, const void* src, uint64_t bytes) {
+  const char* p = static_cast<const char*>(src);
+  while (bytes) {
+    const size_t n = std::fwrite(p, 1, std::min<uint64_t>(bytes, 1ull << 28), f);
+    TGS_CHECK(n > 0, TGS_ERR_INVALID, "checkpoint write failed");
+    p += n;
+    bytes -= n;
+  }
+}
+
+void Table::save(const char* path) {
+  flush();
+  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  std::FILE* f = std::fopen(path, "wb");
+  TGS_CHECK(f, TGS_ERR_INVALID, std::string("cannot open checkpoint for writing: ") + path);
+  try {
+    const uint64_t hdr[7] = {N, B, K, rec_floats, cfg.host_bf16 ? 1ull : 0ull, cfg.moments_policy, stats.steps};
+    ck_write(f, kCkMagic, sizeof(kCkMagic));
+    ck_write(f, hdr, sizeof(hdr));
+    ck_write(f, perm.data(), N * sizeof(uint32_t));
+    ck_write(f, host, K * rec_floats * sizeof(float));
+    std::vector<uint32_t> u(K);
+    TGS_CUDA(cudaMemcpy(u.data(), block_step, K * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    ck_write(f, u.data(), K * sizeof(uint32_t));
+    TGS_CUDA(cudaMemcpy(u.data(), ages, K * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    ck_write(f, u.data(), K * sizeof(uint32_t));
+    std::vector<float4> sp(K);
+    TGS_CUDA(cudaMemcpy(sp.data(), spheres, K * sizeof(float4), cudaMemcpyDeviceToHost));
+    ck_write(f, sp.data(), K * sizeof(float4));
+    TGS_CUDA(cudaMemcpy(sp.data(), spheres_snap, K * sizeof(float4), cudaMemcpyDeviceToHost));
+    ck_write(f, sp.data(), K * sizeof(float4));
+  } catch (...) {
+    std::fclose(f);
+    throw;
+  }
+  TGS_CHECK(std::fclose(f) == 0, TGS_ERR_INVALID, "checkpoint close failed");
+}
+
+void Table::resume(const tgs_config& c, const char* path) {
+  std::FILE* f = std::fopen(path, "rb");
+  TGS_CHECK(f, TGS_ERR_INVALID, std::string("cannot open checkpoint: ") + path);
+  try {
+    char magic[8];
+    ck_read(f, magic, sizeof(magic));
+    TGS_CHECK(std::memcmp(magic, kCkMagic, sizeof(magic)) == 0, TGS_ERR_INVALID, "not a checkpoint file");
+    uint64_t hdr[7];
+    ck_read(f, hdr, sizeof(hdr));
+    TGS_CHECK(hdr[1] == c.block_size && hdr[4] == (c.host_bf16 ? 1ull : 0ull), TGS_ERR_INVALID,
+              "checkpoint block size or record form differs from the configuration");
+    create(c, hdr[0], nullptr, f);
+    TGS_CHECK(hdr[2] == K && hdr[3] == rec_floats, TGS_ERR_INVALID, "checkpoint layout differs");
+    stats.steps = hdr[6];
+  } catch (...) {
+    std::fclose(f);
+    throw;
+  }
+  std::fclose(f);
 }
 
 // Consistency barrier: every dirty resident block goes back to the host tier.

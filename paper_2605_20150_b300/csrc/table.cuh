@@ -1,6 +1,7 @@
 // The block-virtualised training table: pinned host tier, HBM working-set
 // cache, copy streams and the training step (Sec. 3.2-3.5).
 #pragma once
+#include <cstdio>
 #include <vector>
 
 #include <deque>
@@ -10,6 +11,8 @@
 #include "visibility.cuh"
 
 namespace tgs {
+
+void ck_read(std::FILE* f, void* dst, uint64_t bytes);
 
 struct CopyPlan {
   std::vector<uint32_t> early_block, early_slot;  // into free slots, may start now
@@ -73,6 +76,7 @@ struct Table {
   uint32_t* item_touched = nullptr;
   float* grad_local = nullptr;
   float* loss_dev = nullptr;
+  float* ssim_buf = nullptr;       // loss 2: the three D-SSIM partial maps
   float* loss_host = nullptr;
   static constexpr uint64_t LOSS_RING = 4096;
   float* loss_ring = nullptr;      // pinned: the loss sum of the last LOSS_RING steps
@@ -116,17 +120,28 @@ struct Table {
   float pred_threshold = 0.5f;
   uint32_t pred_mask = 1u;
   std::deque<tgs_camera> hist;
+  // exact lookahead (prefetch mode 3): the camera schedule and its cursor
+  static constexpr uint32_t MAX_LOOKAHEAD = 8;
+  uint32_t vis_rows = 0;
+  std::vector<tgs_camera> schedule;
+  uint64_t sched_pos = 0;
+  uint32_t sched_horizon = 0;
   std::vector<uint32_t> r_host_prev;  // resident set before the latest selection
   StageTimer timer;
   StageTimer copy_timer;  // stage 0: H2D batches, stage 1: D2H batches (always on)
 
-  void create(const tgs_config& c, uint64_t n, const float* params_host);
+  // ck (may be null): read the Morton order, host tier and state from a
+  // checkpoint file instead of ordering params_host
+  void create(const tgs_config& c, uint64_t n, const float* params_host, std::FILE* ck = nullptr);
+  void save(const char* path);
+  void resume(const tgs_config& c, const char* path);
   void destroy();
   void fill_host(const float* params);
   void init_spheres();
   void set_params(const float* params);
   void prepare_enqueue(const tgs_camera* cams, uint32_t J, Prepared& out, bool own_batch);
   void prepare_enqueue_predicted(Prepared& out);
+  void prepare_enqueue_lookahead(Prepared& out);
   void select_enqueue(uint32_t J, Prepared& out, bool accessed);
   void cull_only(const tgs_camera* cams, uint32_t J, uint8_t* vis_host);
   void prepare_finish(Prepared& out);
@@ -143,6 +158,8 @@ struct Table {
   // last renders' counts are on the host): grows the pair buffers, counts
   // the dropped steps and clears the flag.  Returns true if one was handled.
   bool check_overflow(bool wait);
+  // the learning rates of the step about to run (schedule at stats.steps)
+  LrSet step_lrs() const;
   // the losses (mean per step) of the steps since the last call, oldest
   // first, at most the last LOSS_RING; waits for the compute stream
   uint64_t losses(float* out, uint64_t max_count);

@@ -291,7 +291,7 @@ def _cols_at(seed, stream, rows, ncol, fn, **kw):
 
 
 def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_width=20.0, ground_frac=0.5,
-                 device="cuda", chunk=1 << 24, near=None):
+                 device="cuda", chunk=1 << 24, near=None, roof_frac=0.0, out_host=None):
     """Synthetic street grid (world z up) of n Gaussians as a float32 torch
     tensor [n, 59] on `device`: roads every 100 m over a side x side square,
     a ground layer (ground_frac of the Gaussians, uniform over the square) and
@@ -299,12 +299,16 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
     block, Gaussians uniform over the facade area).  Log-scales log(spacing/2)
     + N(0, 0.3) with spacing the mean distance between neighbours; opacity
     logit N(2, 0.5); SH DC from a smooth field plus a per-block tint, SH rest
-    N(0, 0.05).  Generated in chunks of `chunk` rows; every value is a
-    function of its row index only.
+    N(0, 0.05).  roof_frac > 0 (the mixed aerial + street city): that
+    fraction of the facade Gaussians lies on the roofs instead (uniform over
+    the block interior at the block's height).  Generated in chunks of
+    `chunk` rows; every value is a function of its row index only.
 
     near=(centre xyz, radius): return only the rows whose mean lies within
     the radius of the centre (bit-identical to those rows of the full table),
-    as (rows [m, 59], row indices [m] int64, spacing)."""
+    as (rows [m, 59], row indices [m] int64, spacing).  out_host (a float32
+    numpy array [n, 59]): the rows are generated on `device` chunk by chunk
+    and copied into it; returns (out_host, spacing)."""
     import torch
     nb = int(side // road_every)
     heights = t_uniform(seed, 40, nb * nb, 10.0, 60.0, device=device)
@@ -314,7 +318,10 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
     ground_area = side * side
     n_ground = int(n * ground_frac)
     spacing = math.sqrt((ground_area + facade_area) / n)
-    out = torch.empty((n, D), dtype=torch.float32, device=device) if near is None else []
+    if out_host is not None:
+        out = None
+    else:
+        out = torch.empty((n, D), dtype=torch.float32, device=device) if near is None else []
     kept = []
     # facade sampling: block by cumulative facade area
     cdf = torch.cumsum(4 * inner * heights, 0)
@@ -342,9 +349,18 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
         y0 = by * road_every - side / 2 + road_width / 2
         fx = torch.where(side_id == 0, x0 + t, torch.where(side_id == 1, x0 + t, torch.where(side_id == 2, x0, x0 + inner)))
         fy = torch.where(side_id == 0, y0, torch.where(side_id == 1, y0 + inner, torch.where(side_id == 2, y0 + t, y0 + t)))
+        fz = u2[f] * h
+        if roof_frac > 0.0:
+            # a draw of its own picks the roof share of the facade rows
+            roof = t_uniform_at(seed, 50, i[f]) < roof_frac
+            rx = x0 + u1[f] * inner
+            ry = y0 + u2[f] * inner
+            fx = torch.where(roof, rx, fx)
+            fy = torch.where(roof, ry, fy)
+            fz = torch.where(roof, h, fz)
         pos[f, 0] = fx
         pos[f, 1] = fy
-        pos[f, 2] = u2[f] * h
+        pos[f, 2] = fz
         if near is not None:
             c = torch.tensor(np.asarray(near[0], np.float64), device=device)
             sel = ((pos.to(torch.float32).to(torch.float64) - c) ** 2).sum(1) < float(near[1]) ** 2
@@ -365,12 +381,16 @@ def street_scene(n=100_000_000, seed=1003, side=4000.0, road_every=100.0, road_w
                            + 0.1 * torch.sin(pos[:, 2] / 7.0 + c) for c in range(3)], 1) + tint[cell]
         rest[:, 0, :] = (col - 0.5) * 3.5
         row[:, 11:59] = rest.reshape(m, 48).to(torch.float32)
-        if near is None:
+        if out_host is not None:
+            out_host[a:a + m] = row.cpu().numpy()
+        elif near is None:
             out[a:a + m] = row
         else:
             out.append(row)
             kept.append(i)
         del pos, rest, col, q, row
+    if out_host is not None:
+        return out_host, spacing
     if near is None:
         return out, spacing
     if not out:
@@ -407,6 +427,44 @@ def street_drive_cameras(n_cams=500, seed=1003, side=4000.0, road_every=100.0, h
             if np.any(np.abs(nxt) > side / 2 - road_every):
                 d = -d
     return cams
+
+
+def lawnmower_cameras(n_cams=1000, side=4000.0, altitude=150.0, pitch_deg=45.0, spacing=400.0, step=8.0,
+                      width=1920, height_px=1080, fov_x=60.0, znear=0.5, zfar=600.0):
+    """An aerial lawnmower path over the square: parallel passes `spacing`
+    apart at `altitude`, `step` metres per frame, the camera looking ahead and
+    down at `pitch_deg`; the passes alternate direction."""
+    cams = []
+    half = side / 2 - spacing / 2
+    y = -half
+    direction = 1.0
+    x = -half
+    t = math.tan(math.radians(pitch_deg))
+    for _ in range(n_cams):
+        p3 = np.array([x, y, altitude])
+        tgt = p3 + np.array([direction, 0.0, -t])
+        R, tv = look_at(p3, tgt, up=(0.0, 0.0, 1.0))
+        cams.append(pinhole(width, height_px, fov_x, R, tv, znear, zfar))
+        x += direction * step
+        if abs(x) > half:
+            x = direction * half
+            direction = -direction
+            y += spacing
+            if y > half:
+                y = -half
+    return cams
+
+
+def city_cameras(n_cams=2000, side=4000.0, seed=1004):
+    """The mixed city trajectory: half aerial lawnmower frames at 1920x1080,
+    half street-drive frames at 1920x1080 (two drives), in that order."""
+    na = n_cams // 2
+    aerial = lawnmower_cameras(na, side=side)
+    nb = n_cams - na
+    d1 = street_drive_cameras(nb // 2, seed=seed, side=side, width=1920, height_px=1080)
+    d2 = street_drive_cameras(nb - nb // 2, seed=seed + 1, side=side, width=1920, height_px=1080, start=(25, 30),
+                              heading=(0.0, -1.0))
+    return aerial + d1 + d2
 
 
 def t_perturb_(rows, seed, row0, mean_std=0.02, logscale_std=0.1, opacity_std=0.5, sh_std=0.05):

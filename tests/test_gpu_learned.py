@@ -26,11 +26,13 @@ def _orbit(n=120):
     return cams
 
 
-def _run(tgs, params, cams, mode, predictor=None, cache=44):
+def _run(tgs, params, cams, mode, predictor=None, cache=44, schedule=False):
     t = tgs.TideTable(params, block_size=250, max_batch=1, max_width=128, max_height=96, cache_blocks=cache,
                       spare_slots=8, prefetch_mode=mode, lr=0.0)
     if predictor is not None:
         t.set_predictor(predictor, threshold=0.3, horizon_mask=0b11)
+    if schedule:
+        t.set_schedule(cams, horizon=2)
     tgt = np.zeros((1, 96, 128, 3), np.float32)
     t.step([cams[0]], tgt, want_loss=False)
     t.sync()
@@ -70,3 +72,17 @@ def test_learned_prefetch_reduces_demand_misses(tgs):
     assert learn["predicted_blocks"] > 0
     assert miss_l < 0.5 * miss_r, (miss_l, miss_r)
     pred.close()
+
+
+def test_exact_lookahead_prefetches_the_trajectory(tgs):
+    """Prefetch mode 3 with the orbit as schedule: the next two cameras' exact
+    visible sets stream ahead, so almost no block is fetched on demand."""
+    cfg = scenes.small_cube_config()
+    cams = _orbit()
+    react = _run(tgs, cfg["params"], cams, 0)
+    look = _run(tgs, cfg["params"], cams, 3, schedule=True)
+    miss_r = react["demand_blocks"] - react["demand_hits"]
+    miss_x = look["demand_blocks"] - look["demand_hits"]
+    assert look["demand_blocks"] == react["demand_blocks"] > 0
+    assert look["predicted_blocks"] > 0
+    assert miss_x <= 0.1 * miss_r, (miss_x, miss_r)

@@ -115,7 +115,7 @@ def _check_step(orc, tgs, params, B, camd, target, loss, W, H, **cfg):
     return len(render_blocks), K
 
 
-@pytest.mark.parametrize("loss", [1, 0])
+@pytest.mark.parametrize("loss", [1, 0, 2])
 def test_step_matches_oracle(orc, tgs, loss):
     c, perm, Pm, cams, targets, table = _setup(orc, tgs, loss=loss)
     table.close()
@@ -216,4 +216,34 @@ def test_render_after_pair_overflow_is_complete(orc, tgs):
     orec = orc.render(Pm.astype(np.float64), scenes.camera_array(camd))
     err, frac = image_within(img.cpu().numpy(), orec)
     assert err <= 1e-4 and frac < 0.05
+    table.close()
+
+
+def test_grouped_learning_rates_follow_the_schedule(orc, tgs):
+    """lr_schedule 1: from zero moments each touched parameter moves by its
+    group's rate times the sign of its gradient (Adam's first step); with a
+    one-step decay the second step's means move by the final rate."""
+    c, perm, Pm, tp = c1_inputs(orc)
+    camd = c["cams"][0]
+    cam = scenes.camera_array(camd)
+    _, Pt = orc.create(tp, 1250)
+    target = orc.render(Pt.astype(np.float64), cam)["img"].astype(np.float32)
+    rates = [1e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3]
+    table = tgs.TideTable(c["params"], block_size=1250, max_batch=1, max_width=256, max_height=256, loss=1,
+                          lr_schedule=1, lr_groups=rates, lr_means_final=1e-5, lr_decay_steps=1)
+    table.step([camd], target[None])
+    p1, m1, _, _ = table.state()
+    d = p1.astype(np.float64) - Pm.astype(np.float64)
+    g = m1.astype(np.float64) / 0.1
+    lr_col = orc.group_lr(rates)
+    big = np.abs(g) > 1e-6 * np.abs(g).max()
+    expect = -np.sign(g) * lr_col[None, :]
+    assert big.sum() > 1000
+    np.testing.assert_allclose(d[big], expect[big], rtol=2e-3, atol=1e-9)
+    # the second step: the means' rate is the final one
+    table.step([camd], target[None])
+    p2, _, _, _ = table.state()
+    step2 = np.abs(p2[:, 0:3].astype(np.float64) - p1[:, 0:3])
+    moved = step2 > 0
+    assert moved.any() and step2[moved].max() <= 1e-5 * 1.5
     table.close()

@@ -120,3 +120,33 @@ def test_async_losses_match_the_synchronous_ones(tgs):
     assert len(b.losses()) == 0
     a.close()
     b.close()
+
+
+def test_checkpoint_resume_continues_training(tgs, tmp_path):
+    """A table checkpointed mid-training and resumed (empty cache, smaller
+    cache size) continues exactly like the original: same losses and state."""
+    cfg = scenes.small_cube_config()
+    cams = _cams()
+    tgt = np.zeros((1, 160, 192, 3), np.float32) + 0.2
+    common = dict(block_size=250, max_batch=1, max_width=192, max_height=160, loss=1, lr=1e-3)
+    a = tgs.TideTable(cfg["params"], cache_blocks=70, spare_slots=4, **common)
+    for i in range(5):
+        a.step([cams[i % 4]], tgt)
+    path = tmp_path / "table.ckpt"
+    a.checkpoint(path)
+    b = tgs.TideTable.resume(path, cache_blocks=60, spare_slots=4, **common)
+    assert b.n == a.n and b.K == a.K
+    pa, ma, va, sa = a.state()
+    pb, mb, vb, sb = b.state()
+    assert np.array_equal(pa, pb) and np.array_equal(ma, mb) and np.array_equal(va, vb) and np.array_equal(sa, sb)
+    assert np.array_equal(a.block_order(), b.block_order())
+    np.testing.assert_array_equal(a.spheres(), b.spheres())
+    la = [a.step([cams[i % 4]], tgt) for i in range(5, 9)]
+    lb = [b.step([cams[i % 4]], tgt) for i in range(5, 9)]
+    np.testing.assert_allclose(lb, la, rtol=1e-5)
+    pa, _, _, sa = a.state()
+    pb, _, _, sb = b.state()
+    assert np.array_equal(sa, sb)
+    assert np.abs(pa.astype(np.float64) - pb).max() < 1e-4
+    a.close()
+    b.close()

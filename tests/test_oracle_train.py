@@ -115,3 +115,31 @@ def test_adam_matches_torch_many_steps(orc):
         opt.step()
         orc.adam(P, G, M1, M2, np.ones(n, np.uint8), np.full(n, s, np.int64), lr=1e-3)
     np.testing.assert_allclose(P, th.detach().numpy(), rtol=0, atol=1e-13)
+
+
+def test_adam_group_rates_match_torch_param_groups(orc):
+    """Per-group learning rates (means, log-scales, rotation, opacity, SH DC,
+    SH rest) agree with torch.optim.Adam over six parameter groups, and the
+    means' rate follows the log-linear 3DGS decay (closed form at both ends and
+    midway the geometric mean)."""
+    import torch
+    rng = np.random.default_rng(4)
+    n = 6
+    rates = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4]
+    P = rng.normal(size=(n, 59))
+    cols = orc.LR_GROUP_COLUMNS
+    ts = [torch.tensor(P[:, a:b].copy(), requires_grad=True) for a, b in cols]
+    opt = torch.optim.Adam([{"params": [t], "lr": r} for t, r in zip(ts, rates)], betas=(0.9, 0.999), eps=1e-15)
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    for s in range(1, 5):
+        G = rng.normal(size=(n, 59))
+        for t, (a, b) in zip(ts, cols):
+            t.grad = torch.tensor(G[:, a:b])
+        opt.step()
+        orc.adam(P, G, M1, M2, np.ones(n, np.uint8), np.full(n, s, np.int64), lr=orc.group_lr(rates))
+    got = np.concatenate([t.detach().numpy() for t in ts], 1)
+    np.testing.assert_allclose(P, got, rtol=0, atol=1e-13)
+    assert orc.lr_schedule_groups(rates, 1.6e-6, 100, 0)[0] == rates[0]
+    assert abs(orc.lr_schedule_groups(rates, 1.6e-6, 100, 100)[0] - 1.6e-6) < 1e-18
+    assert abs(orc.lr_schedule_groups(rates, 1.6e-6, 100, 50)[0] - np.sqrt(1.6e-4 * 1.6e-6)) < 1e-15
+    assert orc.lr_schedule_groups(rates, 1.6e-6, 100, 50)[1:] == rates[1:]
