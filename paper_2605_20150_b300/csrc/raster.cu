@@ -49,14 +49,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// FP32 -> BF16: round to nearest even, or stochastically (add 16 random bits
-// below the kept mantissa, then truncate; unbiased in expectation).
-__device__ __forceinline__ __nv_bfloat16 to_bf16(float x, bool sr, uint64_t key) {
+// FP32 -> BF16: round to nearest even, or stochastically with the 16 random
+// bits r (added below the kept mantissa, then truncated; unbiased in
+// expectation).
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x, bool sr, uint32_t r) {
   if (!sr) return __float2bfloat16_rn(x);
   uint32_t u = __float_as_uint(x);
   if ((u & 0x7F800000u) == 0x7F800000u) return __float2bfloat16_rn(x);
-  uint32_t r = (uint32_t)(mix64(key) & 0xFFFFu);
-  uint32_t v = (u + r) & 0xFFFF0000u;
+  uint32_t v = (u + (r & 0xFFFFu)) & 0xFFFF0000u;
   return __ushort_as_bfloat16((unsigned short)(v >> 16));
 }
 
@@ -961,14 +961,15 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
         float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
         const float upd = lrs.g[lr_group(f)] * (mf * ic1) / (sqrtf(vf * ic2) + eps);
-        const uint64_t key = key0 + (uint64_t)f * 4;
-        m[o] = to_bf16(mf, sr, key);
-        v[o] = to_bf16(vf, sr, key + 1);
+        // one counter hash per field: three 16-bit draws for m, v, parameter
+        const uint64_t hsh = sr ? mix64(key0 + (uint64_t)f) : 0ull;
+        m[o] = to_bf16(mf, sr, (uint32_t)hsh);
+        v[o] = to_bf16(vf, sr, (uint32_t)(hsh >> 16));
         if (f < F_BF16) {
           p[o] -= upd;
         } else {
           const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
-          q16[o16] = to_bf16(__bfloat162float(q16[o16]) - upd, sr, key + 2);
+          q16[o16] = to_bf16(__bfloat162float(q16[o16]) - upd, sr, (uint32_t)(hsh >> 32));
         }
       }
     }
