@@ -259,6 +259,9 @@ typedef struct tgs_stats {
    * because a render of theirs, or of an earlier step not yet seen by the
    * host, overflowed. */
   uint64_t pair_overflows, dropped_steps;
+  /* Host time inside tgs_step, and of it the time blocked on the control
+   * stream's selections (Algorithm 1 lists read back). */
+  double host_step_ms, host_wait_ms;
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
 

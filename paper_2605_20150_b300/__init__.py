@@ -54,7 +54,8 @@ class tgs_stats(ctypes.Structure):
                 ("d2h_ms", ctypes.c_double), ("demand_blocks", ctypes.c_uint64), ("demand_hits", ctypes.c_uint64),
                 ("predicted_blocks", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64),
-                ("pair_overflows", ctypes.c_uint64), ("dropped_steps", ctypes.c_uint64)]
+                ("pair_overflows", ctypes.c_uint64), ("dropped_steps", ctypes.c_uint64),
+                ("host_step_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p

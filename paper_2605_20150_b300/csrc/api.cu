@@ -386,10 +386,12 @@ static void camera_record(CamState& cs, const std::vector<uint32_t>& blocks, uin
   if (t_final) TGS_CUDA(cudaMemcpy(t_final, cs.t_final, pix * sizeof(float), cudaMemcpyDeviceToHost));
   if (n_last) TGS_CUDA(cudaMemcpy(n_last, cs.n_last, pix * sizeof(int), cudaMemcpyDeviceToHost));
   if (grad2d && ng) {
-    std::vector<float> g(9 * cs.cap_v);
-    TGS_CUDA(cudaMemcpy(g.data(), cs.g2, 9 * cs.cap_v * sizeof(float), cudaMemcpyDeviceToHost));
+    const uint64_t st = cs.g2_stride;
+    TGS_CHECK(st >= ng, TGS_ERR_STATE, "no backward for this render list");
+    std::vector<float> g(9 * st);
+    TGS_CUDA(cudaMemcpy(g.data(), cs.g2, 9 * st * sizeof(float), cudaMemcpyDeviceToHost));
     for (uint64_t i = 0; i < ng; ++i)
-      for (int q = 0; q < 9; ++q) grad2d[9 * i + q] = g[(uint64_t)q * cs.cap_v + i];
+      for (int q = 0; q < 9; ++q) grad2d[9 * i + q] = g[(uint64_t)q * st + i];
   }
 }
 

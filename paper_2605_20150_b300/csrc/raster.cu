@@ -584,6 +584,10 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
   // 4 bit4(l) + 2 bit3(l) + bit2(l) of v[0..7]; v[8] by butterfly
   const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
   const int qsel = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+  // the lane's final value, branch-free: b1 (cA A + cC C + cK) + other cB B
+  // (sum 0: A sx + B sy; sum 1: B sx + C sy; conic sums: -1/2, -1, -1/2)
+  const float cA = qsel == 0 ? 1.f : 0.f, cC = qsel == 1 ? 1.f : 0.f, cB = qsel < 2 ? 1.f : 0.f;
+  const float cK = qsel < 2 ? 0.f : (qsel == 3 ? -1.f : (qsel == 2 || qsel == 4 ? -0.5f : 1.f));
   for (int top = wlast; top > 0; top -= 32) {
     // lane l stages list position top - 1 - l: ascending lanes, descending positions
     const int k0 = top - 1 - lane;
@@ -660,11 +664,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         // sums 0 and 1 (lanes l and l ^ 4) swap their sums; conic gradients
         // carry the factors -1/2, -1, -1/2
         const float other = __shfl_xor_sync(0xffffffffu, b1, 4);
-        float fin = b1;
-        if (qsel == 0) fin = a.z * b1 + a.w * other;
-        else if (qsel == 1) fin = a.w * other + bb.x * b1;
-        else if (qsel == 2 || qsel == 4) fin = -0.5f * b1;
-        else if (qsel == 3) fin = -b1;
+        const float fin = b1 * (cA * a.z + cC * bb.x + cK) + other * (cB * a.w);
         const uint32_t id = sp[j].id;
         if ((lane & 3) == 0) {
           if (fin != 0.f) atomicAdd(&g2[(uint64_t)qsel * V + id], fin);
@@ -928,6 +928,9 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
   float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
   float* p = slot + lane;
   if (!BF) {
+    // FP32 record: all loads of the row's fields first (independent, in
+    // flight together), then the updates and stores
+    float gf[ADAM_FG], mf[ADAM_FG], vf[ADAM_FG], pf[ADAM_FG];
     float* m = p + rl.m_off;
     float* v = p + rl.v_off;
 #pragma unroll
@@ -935,15 +938,26 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
       const int f = f0 + q;
       if (f < D) {
         const uint64_t o = (uint64_t)f * B;
-        float gf = grad[(uint64_t)f * V + i];
-        float mf = b1 * m[o] + (1.f - b1) * gf;
-        float vf = b2 * v[o] + (1.f - b2) * gf * gf;
-        m[o] = mf;
-        v[o] = vf;
-        p[o] -= lrs.g[lr_group(f)] * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+        gf[q] = grad[(uint64_t)f * V + i];
+        mf[q] = m[o];
+        vf[q] = v[o];
+        pf[q] = p[o];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        const float mn = b1 * mf[q] + (1.f - b1) * gf[q];
+        const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
+        m[o] = mn;
+        v[o] = vn;
+        p[o] = pf[q] - lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
       }
     }
   } else {
+    // BF16 record: field by field (the two-phase form costs occupancy here)
     __nv_bfloat16* q16 = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
     __nv_bfloat16* m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
     __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
@@ -957,14 +971,14 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
       const int f = f0 + q;
       if (f < D) {
         const uint64_t o = (uint64_t)f * B;
-        float gf = grad[(uint64_t)f * V + i];
-        float mf = b1 * __bfloat162float(m[o]) + (1.f - b1) * gf;
-        float vf = b2 * __bfloat162float(v[o]) + (1.f - b2) * gf * gf;
-        const float upd = lrs.g[lr_group(f)] * (mf * ic1) / (sqrtf(vf * ic2) + eps);
+        const float g = grad[(uint64_t)f * V + i];
+        const float mn = b1 * __bfloat162float(m[o]) + (1.f - b1) * g;
+        const float vn = b2 * __bfloat162float(v[o]) + (1.f - b2) * g * g;
+        const float upd = lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
         // one counter hash per field: three 16-bit draws for m, v, parameter
         const uint64_t hsh = sr ? mix64(key0 + (uint64_t)f) : 0ull;
-        m[o] = to_bf16(mf, sr, (uint32_t)hsh);
-        v[o] = to_bf16(vf, sr, (uint32_t)(hsh >> 16));
+        m[o] = to_bf16(mn, sr, (uint32_t)hsh);
+        v[o] = to_bf16(vn, sr, (uint32_t)(hsh >> 16));
         if (f < F_BF16) {
           p[o] -= upd;
         } else {
@@ -1382,10 +1396,13 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
   const uint64_t V = rl.capacity();
   const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
   if (V == 0) return;
-  TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * cs.cap_v * sizeof(float), s));
+  // the 2D gradients use the render list's size as their stride, so only
+  // that much is cleared (not the whole capacity)
+  cs.g2_stride = V;
+  TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * V * sizeof(float), s));
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
   k_raster_bwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.cap_v,
+                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.g2_stride,
                                                    cs.order_valid ? cs.torder : nullptr);
   TGS_LAUNCHED();
 }
@@ -1397,20 +1414,20 @@ void render_backward_params(const RenderList& rl, const DevCam& cam, const CamSt
   if (rows) {
     const unsigned grid = std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM);
     if (rl.bf16)
-      k_preprocess_bwd<true><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v, grad,
+      k_preprocess_bwd<true><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.g2_stride, grad,
                                                         rl.capacity(), mode, cpi, rows, nrows);
     else
-      k_preprocess_bwd<false><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.cap_v, grad,
+      k_preprocess_bwd<false><<<grid, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2, cs.g2_stride, grad,
                                                          rl.capacity(), mode, cpi, rows, nrows);
     TGS_LAUNCHED();
     return;
   }
   if (rl.bf16)
     k_preprocess_bwd<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                  cs.cap_v, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
+                                                                  cs.g2_stride, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
   else
     k_preprocess_bwd<false><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, cs.ntiles, cs.rgb, cs.conic_o, cs.g2,
-                                                                   cs.cap_v, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
+                                                                   cs.g2_stride, grad, rl.capacity(), mode, cpi, nullptr, nullptr);
   TGS_LAUNCHED();
 }
 

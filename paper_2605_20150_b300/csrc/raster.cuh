@@ -48,7 +48,8 @@ struct CamState {
   uint32_t* scan = nullptr;    // V: visibility scan, then pair offsets
   uint32_t* dkeys = nullptr;   // V x 2 (ping-pong): depth keys / positions
   uint32_t* dvals = nullptr;
-  float* g2 = nullptr;         // 9 x V: dL/d(u, v, A, B, C, opacity, r, g, b)
+  float* g2 = nullptr;         // 9 x g2_stride: dL/d(u, v, A, B, C, opacity, r, g, b)
+  uint64_t g2_stride = 0;      // the last backward's render-list size
   // per pair
   uint32_t* pkeys = nullptr;   // 2 x cap_pairs (ping-pong)
   uint32_t* pvals = nullptr;

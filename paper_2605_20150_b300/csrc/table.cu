@@ -8,6 +8,7 @@
 // computes (Sec. 3.4 "Hierarchical asynchronous execution"); blocks that can
 // only go into slots freed by S- are copied after that write-back.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -420,7 +421,9 @@ void Table::select_enqueue(uint32_t J, Prepared& out, bool accessed) {
   if (quota * J > C) quota = C / J;
   residency(acc_bits, r_bits, kvis, kvis_union, (int)J, K, ages, C, cfg.lambda, quota, r_next_bits,
             lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl, accessed);
+  // counts and the three lists in full (one read-back, one host wait)
   TGS_CUDA(cudaMemcpyAsync(lists_host, rb.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  TGS_CUDA(cudaMemcpyAsync(lists_host + 16, lists_dev, 3 * K * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
   TGS_CUDA(cudaMemcpyAsync(kvis_host_pinned, kvis, (uint64_t)J * words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                            ctl));
   TGS_CUDA(cudaEventRecord(ev_ctl, ctl));
@@ -446,25 +449,24 @@ void Table::cull_only(const tgs_camera* cs, uint32_t J, uint8_t* vis_host) {
     for (uint64_t k = 0; k < K; ++k) vis_host[(uint64_t)j * K + k] = (w[(uint64_t)j * words + (k >> 5)] >> (k & 31)) & 1u;
 }
 
+// Host time blocked on the control stream (tracing counter).
+void Table::wait_ctl() {
+  const auto t0 = std::chrono::steady_clock::now();
+  TGS_CUDA(cudaStreamSynchronize(ctl));
+  stats.host_wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 void Table::prepare_finish(Prepared& out) {
   TGS_CHECK(out.enqueued, TGS_ERR_STATE, "prepare_finish without prepare_enqueue");
-  TGS_CUDA(cudaStreamSynchronize(ctl));
+  wait_ctl();
   const uint32_t J = (uint32_t)out.cams.size();
   const uint32_t np = lists_host[0], nm = lists_host[1], nr = lists_host[2];
   out.kvis_host.assign(kvis_host_pinned, kvis_host_pinned + (uint64_t)J * words);
   out.r_host.assign(r_host_pinned, r_host_pinned + words);
-  uint32_t cnts[3] = {np, nm, nr};
-  uint64_t off = 0;
-  for (int q = 0; q < 3; ++q) {
-    if (cnts[q])
-      TGS_CUDA(cudaMemcpyAsync(lists_host + off, lists_dev + (uint64_t)q * K, cnts[q] * sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, ctl));
-    off += cnts[q];
-  }
-  TGS_CUDA(cudaStreamSynchronize(ctl));
-  out.s_plus.assign(lists_host, lists_host + np);
-  out.s_minus.assign(lists_host + np, lists_host + np + nm);
-  out.render_blocks.assign(lists_host + np + nm, lists_host + np + nm + nr);
+  const uint32_t* lists = lists_host + 16;
+  out.s_plus.assign(lists, lists + np);
+  out.s_minus.assign(lists + K, lists + K + nm);
+  out.render_blocks.assign(lists + 2 * K, lists + 2 * K + nr);
   // demand hit counters: blocks of an actual batch already resident before
   // its selection (for the learned mode: after the prediction's copies)
   if (!out.predicted) {
@@ -741,6 +743,15 @@ static bool same_cams(const std::vector<tgs_camera>& a, const tgs_camera* b, uin
 void Table::step(const tgs_camera* cs, uint32_t J, const tgs_camera* next, uint32_t nJ, const float* targets_dev,
                  const float* targets_host, cudaStream_t user, float* loss_out) {
   TGS_CHECK(cs && J >= 1, TGS_ERR_INVALID, "tgs_step: no cameras");
+  const auto t_step = std::chrono::steady_clock::now();
+  struct StepClock {
+    Table& t;
+    std::chrono::steady_clock::time_point t0;
+    ~StepClock() {
+      t.stats.host_step_ms +=
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  } step_clock{*this, t_step};
   check_overflow(false);
   if (!(prep.valid && same_cams(prep.cams, cs, J))) {
     // reactive path: select and stream this batch's working set now

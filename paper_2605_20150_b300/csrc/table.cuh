@@ -154,6 +154,7 @@ struct Table {
   void render(const tgs_camera& cam, float* image_dev, cudaStream_t user);
   void flush();
   void collect_stall();
+  void wait_ctl();
   // Handles a pair-capacity overflow seen by a render (wait: block until the
   // last renders' counts are on the host): grows the pair buffers, counts
   // the dropped steps and clears the flag.  Returns true if one was handled.

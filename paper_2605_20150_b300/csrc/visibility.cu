@@ -202,6 +202,244 @@ __global__ void k_res_lists(const uint32_t* __restrict__ r_next, const uint32_t*
   }
 }
 
+
+// ---- Algorithm 1 in one CTA (K <= SEL_MAX_K): the same selection as the
+// multi-kernel path below, in shared memory, so a selection costs one launch
+// (the control stream's kernels otherwise each wait for a free SM slot behind
+// the compute stream's raster CTAs).
+//
+// Scores take at most 254 values (visibility flag x age 0..126): candidates
+// are ordered by a stable counting sort on the rank of their FP32 score among
+// the distinct score values (descending; equal scores share a rank, so ties
+// resolve to the lower block id, as in the stable sort by score bits).
+constexpr int SEL_THREADS = 1024;
+constexpr int SEL_WARPS = SEL_THREADS / 32;
+constexpr int SEL_BUCKETS = 254;  // visibility flag x 127 ages
+constexpr int SEL_MAX_K = 65536;
+
+__device__ __forceinline__ float res_score(int kn, uint32_t a, float lam) {
+  const float oml = __fsub_rn(1.f, lam);
+  const float t = __fmul_rn(oml, ldexpf(1.f, -(int)a));
+  return __fadd_rn(kn ? lam : 0.f, t);
+}
+
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t x, uint32_t* sw, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sw[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = sw[lane];
+    uint32_t vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    sw[lane] = vi - v;
+    if (lane == 31) sw[32] = vi;
+  }
+  __syncthreads();
+  const uint32_t r = sw[w] + inc - x;
+  if (total) *total = sw[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select_small(
+    const uint32_t* __restrict__ k_acc, const uint32_t* __restrict__ r_cur, const uint32_t* __restrict__ k_next,
+    const uint32_t* __restrict__ k_union, int J, uint32_t K, uint32_t* __restrict__ ages, float lambda,
+    int age_update, uint32_t capacity, uint32_t quota, uint32_t* __restrict__ r_next,
+    uint32_t* __restrict__ s_plus, uint32_t* __restrict__ s_minus, uint32_t* __restrict__ render,
+    uint32_t* __restrict__ acc_out, uint32_t* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t words = (K + 31) / 32;
+  uint16_t* ids = reinterpret_cast<uint16_t*>(smem);                           // sorted candidates
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + 2 * SEL_MAX_K);          // [warps][buckets]
+  uint32_t* selb = hist + SEL_WARPS * 256;                                     // selected (sorted index bits)
+  uint32_t* rnb = selb + SEL_MAX_K / 32;                                       // r_next bits
+  __shared__ uint16_t rank_of[SEL_BUCKETS];
+  __shared__ float score_of[SEL_BUCKETS];
+  __shared__ uint8_t first_of[SEL_BUCKETS];
+  __shared__ uint32_t sw[33];
+  __shared__ uint32_t s_nr, s_ncand, s_nsel;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+
+  // score of every bucket and its rank among the distinct scores (descending)
+  if (tid < SEL_BUCKETS) score_of[tid] = res_score(tid >= 127, (uint32_t)(tid % 127), lambda);
+  for (uint32_t e = tid; e < SEL_WARPS * 256; e += SEL_THREADS) hist[e] = 0;
+  for (uint32_t e = tid; e < SEL_MAX_K / 32; e += SEL_THREADS) selb[e] = 0;
+  for (uint32_t e = tid; e < words; e += SEL_THREADS) rnb[e] = 0;
+  __syncthreads();
+  // first_of[b]: b is the first bucket with its score value
+  if (tid < SEL_BUCKETS) {
+    const float sc = score_of[tid];
+    bool first = true;
+    for (int c = 0; c < tid; ++c)
+      if (score_of[c] == sc) first = false;
+    first_of[tid] = first ? 1 : 0;
+  }
+  __syncthreads();
+  if (tid < SEL_BUCKETS) {
+    const float sc = score_of[tid];
+    uint32_t r = 0;
+    for (int b = 0; b < SEL_BUCKETS; ++b)
+      if (first_of[b] && score_of[b] > sc) ++r;
+    rank_of[tid] = (uint16_t)r;
+  }
+  __syncthreads();
+
+  // ages, candidate flags, per-warp histograms of score ranks (warp w walks the
+  // contiguous id range [w * chunk, (w + 1) * chunk) 32 ids at a time)
+  const uint32_t chunk = ((K + SEL_WARPS - 1) / SEL_WARPS + 31) / 32 * 32;
+  const uint32_t k_lo = wid * chunk, k_hi = min(K, k_lo + chunk);
+  for (uint32_t k0 = k_lo; k0 < k_hi; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    bool cand = false;
+    uint32_t bkt = 0;
+    if (k < k_hi) {
+      uint32_t a = ages[k];
+      const bool r = (r_cur[k >> 5] >> (k & 31)) & 1u, kn = (k_union[k >> 5] >> (k & 31)) & 1u;
+      if (age_update) {
+        if (r && ((k_acc[k >> 5] >> (k & 31)) & 1u)) a = 0;
+        else if (a < 126) a += 1;
+        ages[k] = a;
+      }
+      cand = r || kn;
+      bkt = (kn ? 127u : 0u) + a;
+    }
+    if (cand) atomicAdd(&hist[wid * 256 + rank_of[bkt]], 1u);
+  }
+  __syncthreads();
+  // offsets: rank-major, then warp order
+  if (tid == 0) {
+    uint32_t nr = 0;
+    for (int b = 0; b < SEL_BUCKETS; ++b) nr = max(nr, (uint32_t)rank_of[b] + 1u);
+    s_nr = nr;
+  }
+  __syncthreads();
+  {
+    uint32_t tot = 0;
+    if (tid < (int)s_nr)
+      for (int w = 0; w < SEL_WARPS; ++w) {
+        const uint32_t c = hist[w * 256 + tid];
+        hist[w * 256 + tid] = tot;
+        tot += c;
+      }
+    uint32_t n;
+    const uint32_t base = block_scan_excl(tid < (int)s_nr ? tot : 0u, sw, &n);
+    if (tid < (int)s_nr)
+      for (int w = 0; w < SEL_WARPS; ++w) hist[w * 256 + tid] += base;
+    if (tid == 0) s_ncand = n;
+  }
+  __syncthreads();
+  // stable placement: within a warp's group of 32 ids, earlier lanes of equal
+  // rank first (match_any), the warp's running offset per rank in hist
+  for (uint32_t k0 = k_lo; k0 < k_hi; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    bool cand = false;
+    uint32_t rk = 0xFFFFu;
+    if (k < k_hi) {
+      const uint32_t a = ages[k];  // already updated by this lane
+      const bool r = (r_cur[k >> 5] >> (k & 31)) & 1u, kn = (k_union[k >> 5] >> (k & 31)) & 1u;
+      cand = r || kn;
+      if (cand) rk = rank_of[(kn ? 127u : 0u) + a];
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, rk);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader && cand) {
+      base = hist[wid * 256 + rk];
+      hist[wid * 256 + rk] = base + __popc(peers);
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cand) ids[base + __popc(peers & lt)] = (uint16_t)k;
+    __syncwarp();
+  }
+  __syncthreads();
+  const uint32_t nc = s_ncand;
+
+  // camera-balanced quota: per camera, the first `quota` of its visible
+  // candidates in sorted order
+  for (int j = 0; j < J; ++j) {
+    const uint32_t* kj = k_next + (uint64_t)j * words;
+    uint32_t carry = 0;
+    for (uint32_t s0 = 0; s0 < nc; s0 += SEL_THREADS) {
+      const uint32_t s = s0 + tid;
+      const uint32_t f = s < nc ? (kj[ids[s] >> 5] >> (ids[s] & 31)) & 1u : 0u;
+      uint32_t tot;
+      const uint32_t pre = block_scan_excl(f, sw, &tot) + carry;
+      if (f && pre < quota) atomicOr(&selb[s >> 5], 1u << (s & 31));
+      carry += tot;
+    }
+    __syncthreads();
+  }
+  // global fill in sorted order up to the capacity
+  {
+    uint32_t nsel = 0;
+    for (uint32_t e = tid; e < (nc + 31) / 32; e += SEL_THREADS) nsel += __popc(selb[e]);
+    uint32_t tot;
+    block_scan_excl(nsel, sw, &tot);
+    nsel = tot;
+    uint32_t carry = 0;
+    for (uint32_t s0 = 0; s0 < nc; s0 += SEL_THREADS) {
+      const uint32_t s = s0 + tid;
+      const bool sel = s < nc && ((selb[s >> 5] >> (s & 31)) & 1u);
+      const uint32_t un = (s < nc && !sel) ? 1u : 0u;
+      uint32_t t2;
+      const uint32_t pre = block_scan_excl(un, sw, &t2) + carry;
+      const bool take = sel || (un && nsel < capacity && pre < capacity - nsel);
+      if (take) atomicOr(&rnb[ids[s] >> 5], 1u << (ids[s] & 31));
+      carry += t2;
+    }
+    if (tid == 0) s_nsel = nsel;
+  }
+  __syncthreads();
+  // S+ = r_next & ~r_cur, S- = r_cur & ~r_next, render = r_next & K_union, in
+  // ascending block id
+  uint32_t off[3] = {0, 0, 0};
+  uint32_t* outs[3] = {s_plus, s_minus, render};
+  for (uint32_t w0 = 0; w0 < words; w0 += SEL_THREADS) {
+    const uint32_t w = w0 + tid;
+    uint32_t m[3] = {0, 0, 0};
+    if (w < words) {
+      const uint32_t rn = rnb[w], rc = r_cur[w];
+      m[0] = rn & ~rc;
+      m[1] = rc & ~rn;
+      m[2] = rn & k_union[w];
+      r_next[w] = rn;
+      acc_out[w] = m[2];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      uint32_t tot;
+      uint32_t o = block_scan_excl(__popc(m[q]), sw, &tot) + off[q];
+      uint32_t mm = m[q];
+      while (mm) {
+        const int b = __ffs(mm) - 1;
+        outs[q][o++] = w * 32 + b;
+        mm &= mm - 1;
+      }
+      off[q] += tot;
+    }
+  }
+  if (tid == 0) {
+    counters[0] = off[0];
+    counters[1] = off[1];
+    counters[2] = off[2];
+    counters[3] = nc;
+    counters[4] = s_nsel;
+  }
+}
+
+size_t select_small_smem() { return 2 * SEL_MAX_K + (SEL_WARPS * 256 + SEL_MAX_K / 32 + SEL_MAX_K / 32) * 4; }
+
 }  // namespace
 
 Planes frustum_planes(const tgs_camera& c, float m) {
@@ -283,6 +521,15 @@ void residency(const uint32_t* k_acc, const uint32_t* r_cur, const uint32_t* k_n
                uint32_t* s_plus, uint32_t* s_minus, uint32_t* render, uint32_t* acc_out, ResidencyBuffers& rb,
                cudaStream_t s, bool age_update) {
   const uint64_t words = (K + 31) / 32;
+  if (K <= SEL_MAX_K && J <= 8) {
+    TGS_CUDA(cudaFuncSetAttribute(k_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)select_small_smem()));
+    k_select_small<<<1, SEL_THREADS, select_small_smem(), s>>>(
+        k_acc, r_cur, k_next, k_next_union, J, (uint32_t)K, ages, lambda, age_update ? 1 : 0, (uint32_t)capacity,
+        (uint32_t)quota, r_next, s_plus, s_minus, render, acc_out, rb.counters);
+    TGS_LAUNCHED();
+    return;
+  }
   const unsigned gk = div_up(K, 256);
   uint32_t* cnt = rb.counters;
   k_res_score<<<gk, 256, 0, s>>>(k_acc, r_cur, k_next_union, K, ages, lambda, age_update ? 1 : 0, rb.flag, rb.tmp);
