@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cams", type=int, default=None)
     ap.add_argument("--cache-gb", type=float, default=24.0, help="HBM working-set cache cap (street workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="street: also time the Tab. 5 ablations (no differential streaming, no overlap, no Morton)")
     return ap.parse_args()
 
 
@@ -366,6 +368,7 @@ def run_street(args, rank, world, local):
     tb.set_prefetch_mode(2)
     head = forms["bf16_learned"]
     drive_b = drive_b_eval(args, tgs, tb, pred, host, base, dev)
+    ablation = ablation_eval(args, tgs, host, base, cams, targets, train_ids) if args.ablation else None
     peak = link_peak(torch)
     # end to end (headline form) with host targets and the loss read back each step
     host_t = torch.empty(min(nc, 64), H, W, 3, dtype=torch.float32, pin_memory=True)
@@ -415,7 +418,59 @@ def run_street(args, rank, world, local):
     out["_pred"] = pred
     out["bf16"] = True
     out["drive_b"] = drive_b
+    out["ablation"] = ablation
     return out
+
+
+def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=40, warm=5):
+    """Tab. 5 analogue on the street scene (BF16 record, exact next-batch
+    prefetch as the full method): the same n steps with differential streaming
+    off (every selection evicts the cache and streams the selected set again),
+    with copy/compute overlap off, and with blocks in input order instead of
+    Morton order."""
+    import torch
+    variants = [("full", {}), ("no_differential", {"differential": 0}), ("no_overlap", {"overlap": 0}),
+                ("no_morton", {"morton": 0})]
+    res = {}
+    for name, kw in variants:
+        cfg = dict(base)
+        cfg.update(prefetch_mode=1, host_bf16=1, stochastic_round=1)
+        cfg.update(kw)
+        if name == "no_morton":
+            # runs of the input order span the whole city: a batch touches far
+            # more blocks than the cache holds at the street setting
+            cfg["cache_blocks"] = int(cfg["cache_blocks"])
+        t = tgs.TideTable(host, **cfg)
+        seq = train_ids
+
+        def one(k):
+            i, j = seq[k % len(seq)], seq[(k + 1) % len(seq)]
+            t.step([cams[i]], targets[i:i + 1], next_cams=[cams[j]], want_loss=False)
+
+        try:
+            for k in range(warm):
+                one(k)
+            t.sync()
+            s0 = t.stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(warm, warm + n):
+                one(k)
+            e1.record()
+            t.sync()
+            torch.cuda.synchronize()
+            st = t.stats()
+            ms = e0.elapsed_time(e1) / n
+            res[name] = {"ms_per_step": round(ms, 3), "iters_per_s": round(1e3 / ms, 2),
+                         "h2d_gb_per_step": round((st["bytes_h2d"] - s0["bytes_h2d"]) / n / 1e9, 4),
+                         "d2h_gb_per_step": round((st["bytes_d2h"] - s0["bytes_d2h"]) / n / 1e9, 4),
+                         "stall_ms_per_step": round((st["stall_ms"] - s0["stall_ms"]) / n, 3),
+                         "render_blocks": st["last_render_blocks"]}
+        except Exception as e:  # a variant that does not fit the configuration
+            res[name] = {"error": str(e)[:200]}
+        t.close()
+    res["steps"] = n
+    return res
 
 
 def drive_b_eval(args, tgs, tb, pred, host, base, dev, n=100):
@@ -842,6 +897,8 @@ def main():
         line["psnr_gap_db"] = res["psnr_gap_db"]
         line["vs_fp32_reactive"] = round(value / max(res["forms"]["fp32_reactive"]["iters_per_s"], 1e-9), 4)
         line["drive_b"] = res["drive_b"]
+        if res.get("ablation"):
+            line["ablation"] = res["ablation"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not city:
         line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()

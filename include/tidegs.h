@@ -110,6 +110,12 @@ typedef struct tgs_config {
   float lr_groups[6];
   float lr_means_final;
   uint32_t lr_decay_steps;
+  /* Ablations (Tab. 5): differential 0 = every selection evicts the whole
+   * cache and streams the selected set again ("w/o Tide"); morton 0 = blocks
+   * are runs of the input order ("w/o Morton").  overlap 0 above is "w/o
+   * Overlap". */
+  uint32_t differential;
+  uint32_t morton;
 } tgs_config;
 
 void tgs_default_config(tgs_config* cfg);

@@ -43,7 +43,7 @@ class tgs_config(ctypes.Structure):
                 ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32),
                 ("pair_capacity", ctypes.c_uint64), ("max_render_blocks", ctypes.c_uint64),
                 ("lr_schedule", ctypes.c_uint32), ("lr_groups", ctypes.c_float * 6), ("lr_means_final", ctypes.c_float),
-                ("lr_decay_steps", ctypes.c_uint32)]
+                ("lr_decay_steps", ctypes.c_uint32), ("differential", ctypes.c_uint32), ("morton", ctypes.c_uint32)]
 
 
 class tgs_stats(ctypes.Structure):

@@ -127,6 +127,8 @@ void tgs_default_config(tgs_config* c) {
   for (int i = 0; i < 6; ++i) c->lr_groups[i] = g[i];
   c->lr_means_final = 1.6e-6f;
   c->lr_decay_steps = 30000;
+  c->differential = 1;
+  c->morton = 1;
 }
 
 tgs_status tgs_create(const tgs_config* cfg, uint64_t n, const float* params_host, tgs_table** out) {

@@ -354,16 +354,64 @@ __global__ void __launch_bounds__(EP_THREADS) k_emit_pairs(const uint32_t* __res
 }
 
 // Tile order of the raster launches, longest pair list first (so the long
-// tiles do not start last): key 65535 - min(length, 65535), stable.
-__global__ void k_tile_keys(const uint2* __restrict__ ranges, uint32_t tiles, uint32_t* __restrict__ keys,
-                            uint32_t* __restrict__ vals, uint32_t* __restrict__ n_out) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) *n_out = tiles;
-  if (t >= tiles) return;
-  const uint2 r = ranges[t];
-  const uint32_t len = r.y - r.x;
-  keys[t] = 0xFFFFu - (len < 0xFFFFu ? len : 0xFFFFu);
-  vals[t] = t;
+// tiles do not start last), in one CTA: a stable counting sort of the tiles on
+// a logarithmic length bucket (255 - 16 log2(1 + length), clamped to 0..255);
+// the order is a scheduling heuristic, so bucket ties keep tile order.
+constexpr int TO_THREADS = 1024;
+__global__ void __launch_bounds__(TO_THREADS) k_tile_order(const uint2* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ order) {
+  __shared__ uint32_t cnt[32][256];
+  __shared__ uint32_t base[256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < 32 * 256; e += TO_THREADS) (&cnt[0][0])[e] = 0;
+  __syncthreads();
+  // warp w owns the tiles [w * per, (w + 1) * per), 32 at a time
+  const uint32_t per = ((tiles + 31) / 32 + 31) / 32 * 32;
+  const uint32_t t_lo = w * per, t_hi = min(tiles, t_lo + per);
+  auto bucket = [&](uint32_t t) {
+    const uint2 r = ranges[t];
+    const float l = log2f(1.f + (float)(r.y - r.x));
+    const int b = 255 - (int)(16.f * l);
+    return (uint32_t)(b < 0 ? 0 : b);
+  };
+  for (uint32_t t0 = t_lo; t0 < t_hi; t0 += 32)
+    if (t0 + lane < t_hi) atomicAdd(&cnt[w][bucket(t0 + lane)], 1u);
+  __syncthreads();
+  if (tid < 256) {
+    uint32_t run = 0;
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t c = cnt[k][tid];
+      cnt[k][tid] = run;
+      run += c;
+    }
+    base[tid] = run;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < 256; ++b) {
+      const uint32_t c = base[b];
+      base[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t t0 = t_lo; t0 < t_hi; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    const bool ok = t < t_hi;
+    const uint32_t b = ok ? bucket(t) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t o = 0;
+    if (lane == leader && ok) {
+      o = cnt[w][b];
+      cnt[w][b] = o + __popc(peers);
+    }
+    o = __shfl_sync(0xffffffffu, o, leader);
+    if (ok) order[base[b] + o + __popc(peers & lt)] = t;
+    __syncwarp();
+  }
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, const uint32_t* __restrict__ pkeys,
@@ -1293,10 +1341,8 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
                          bits_for(tiles), cs.scratch, s, cs.hint_np);
     k_ranges<<<2 * NSM, 256, 0, s>>>(np_dev, cs.cap_pairs, cs.pkeys, cs.ranges);
     TGS_LAUNCHED();
-    k_tile_keys<<<div_up(tiles, 256), 256, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.tkeys, cs.torder, cs.counters + 4);
+    k_tile_order<<<1, TO_THREADS, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.torder);
     TGS_LAUNCHED();
-    radix_sort_pairs_dev(cs.tkeys, cs.torder, cs.tkeys + cs.cap_tiles, cs.torder + cs.cap_tiles, cs.counters + 4,
-                         tiles, 16, cs.scratch, s);
     cs.order_valid = true;
     tm->end(StageTimer::SORT, s);
   } else {

@@ -130,12 +130,17 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
       dalloc(pm, 2 * N);
       TGS_CUDA(cudaMalloc(&scr, radix_scratch_bytes(N)));
       dalloc(aabb, 16);
-      TGS_CUDA(cudaMemcpy2DAsync(means, 3 * sizeof(float), params, D * sizeof(float), 3 * sizeof(float), N,
-                                 cudaMemcpyHostToDevice, comp));
-      morton_order(means, N, pm, codes, codes + N, pm + N, scr, aabb, comp);
       perm.resize(N);
-      TGS_CUDA(cudaMemcpyAsync(perm.data(), pm, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, comp));
-      TGS_CUDA(cudaStreamSynchronize(comp));
+      if (c.morton) {
+        TGS_CUDA(cudaMemcpy2DAsync(means, 3 * sizeof(float), params, D * sizeof(float), 3 * sizeof(float), N,
+                                   cudaMemcpyHostToDevice, comp));
+        morton_order(means, N, pm, codes, codes + N, pm + N, scr, aabb, comp);
+        TGS_CUDA(cudaMemcpyAsync(perm.data(), pm, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, comp));
+        TGS_CUDA(cudaStreamSynchronize(comp));
+      } else {
+        // ablation (Tab. 5 "w/o Morton"): blocks are runs of the input order
+        for (uint64_t g = 0; g < N; ++g) perm[g] = (uint32_t)g;
+      }
       dfree(means); dfree(codes); dfree(pm); dfree(scr); dfree(aabb);
     }
   }
@@ -467,6 +472,17 @@ void Table::prepare_finish(Prepared& out) {
   out.s_plus.assign(lists, lists + np);
   out.s_minus.assign(lists + K, lists + K + nm);
   out.render_blocks.assign(lists + 2 * K, lists + 2 * K + nr);
+  if (!cfg.differential && !out.predicted) {
+    // ablation (Tab. 5 "w/o Tide"): no differential streaming -- every
+    // resident block leaves (dirty ones written back) and the whole selected
+    // set streams in again
+    out.s_minus.clear();
+    for (uint64_t b = 0; b < K; ++b)
+      if (slot_of[b] >= 0) out.s_minus.push_back((uint32_t)b);
+    out.s_plus.clear();
+    for (uint64_t w = 0; w < words; ++w)
+      for (uint32_t m = out.r_host[w]; m; m &= m - 1) out.s_plus.push_back((uint32_t)(w * 32 + __builtin_ctz(m)));
+  }
   // demand hit counters: blocks of an actual batch already resident before
   // its selection (for the learned mode: after the prediction's copies)
   if (!out.predicted) {
@@ -506,6 +522,14 @@ void Table::prepare_finish(Prepared& out) {
       pl.late_block.push_back(b);
       pl.late_slot.push_back(ev_slots[ei++]);
     }
+  }
+  if (!cfg.differential) {
+    // a block may leave and come back in the same selection: every load goes
+    // after the write-backs (late), so a reload sees its written-back record
+    pl.late_block.insert(pl.late_block.begin(), pl.early_block.begin(), pl.early_block.end());
+    pl.late_slot.insert(pl.late_slot.begin(), pl.early_slot.begin(), pl.early_slot.end());
+    pl.early_block.clear();
+    pl.early_slot.clear();
   }
   // host mirrors describe the state after this selection's copies
   for (size_t i = 0; i < pl.evict_block.size(); ++i) {

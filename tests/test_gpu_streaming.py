@@ -150,3 +150,47 @@ def test_checkpoint_resume_continues_training(tgs, tmp_path):
     assert np.abs(pa.astype(np.float64) - pb).max() < 1e-4
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prefetch", [1, 0])
+def test_ablation_without_differential_streaming_trains_identically(tgs, prefetch):
+    """differential = 0 re-streams the whole selected set every step (dirty
+    blocks written back first): same losses and state, far more traffic."""
+    cfg = scenes.small_cube_config()
+    cams = _cams()
+    tgt = np.zeros((1, 160, 192, 3), np.float32) + 0.2
+    common = dict(block_size=250, max_batch=1, max_width=192, max_height=160, loss=1, lr=1e-3, cache_blocks=60,
+                  spare_slots=4, prefetch_mode=prefetch)
+    a = tgs.TideTable(cfg["params"], **common)
+    b = tgs.TideTable(cfg["params"], differential=0, **common)
+    seq = [cams[i % 4] for i in range(7)]
+    la = [a.step([c], tgt, next_cams=[seq[i + 1]] if i + 1 < len(seq) else None) for i, c in enumerate(seq)]
+    lb = [b.step([c], tgt, next_cams=[seq[i + 1]] if i + 1 < len(seq) else None) for i, c in enumerate(seq)]
+    np.testing.assert_allclose(lb, la, rtol=1e-5)
+    pa, _, _, sa = a.state()
+    pb, _, _, sb = b.state()
+    assert np.array_equal(sa, sb) and np.abs(pa.astype(np.float64) - pb).max() < 1e-4
+    assert b.stats()["bytes_h2d"] > 2 * a.stats()["bytes_h2d"]
+    a.close()
+    b.close()
+
+
+def test_ablation_without_morton_order_renders_the_same_image(tgs):
+    """morton = 0 keeps the input order in the blocks: with every block
+    resident the render is the same image (blocks only change what is culled
+    and streamed), up to the order of splats with equal FP32 depth, which
+    resolves by render-list position."""
+    import torch
+    cfg = scenes.small_cube_config()
+    cam = _cams()[0]
+    imgs = []
+    for morton in (1, 0):
+        t = tgs.TideTable(cfg["params"], block_size=250, max_batch=1, max_width=192, max_height=160, morton=morton)
+        img = torch.zeros(160, 192, 3, device="cuda")
+        t.render(cam, img)
+        imgs.append(img.cpu().numpy())
+        if morton == 0:
+            assert np.array_equal(t.block_order(), np.arange(t.n))
+        t.close()
+    d = np.abs(imgs[0] - imgs[1])
+    assert d.max() < 1e-3 and (d > 1e-6).mean() < 0.01
