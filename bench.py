@@ -407,6 +407,7 @@ def run_street(args, rank, world, local):
                       "stall_ms_per_step": round(dd["stall_ms"] / args.steps, 4),
                       "demand_hit_rate": round(dd["demand_hits"] / max(dd["demand_blocks"], 1), 5),
                       "predicted_blocks_per_step": dd["predicted_blocks"] / args.steps,
+                      "stages_ms_per_step": {s: round(v[0] / args.steps, 4) for s, v in f["stages"].items()},
                       "host_ms_per_step": round(dd["host_step_ms"] / args.steps, 4),
                       "host_wait_ms_per_step": round(dd["host_wait_ms"] / args.steps, 4),
                       "readmissions": dd["readmissions"], "writebacks": dd["writebacks"]}

@@ -455,21 +455,32 @@ __device__ __forceinline__ WarpPix warp_pixels(int tile, int TX) {
   return q;
 }
 
-// Half-sizes of the axis-aligned box containing every pixel offset d with
-// alpha >= 1/255: d^T K d <= 2 ln(255 o) with K the conic (A, B, C), so
-// |dx| <= sqrt(2 L (K^-1)_xx).  Widened by a relative 1e-3 and 0.05 px; a
-// negative value means the splat can never reach 1/255.
-__device__ __forceinline__ float2 alpha_box(float A, float B, float C, float o) {
-  const float L = logf(255.f * o);
-  if (!(L > 0.f)) return make_float2(-1.f, -1.f);
-  const float det = A * C - B * B;
-  const float s = 2.002f * L / det;
-  return make_float2(sqrtf(fmaxf(s * C, 0.f)) + 0.05f, sqrtf(fmaxf(s * A, 0.f)) + 0.05f);
+// The region where a splat's alpha reaches 1/255 meets the warp's square:
+// alpha >= 1/255 iff qf(d) = A dx^2 + 2 B dx dy + C dy^2 <= 2 ln(255 o), and
+// the minimum of that convex quadratic over the square [wx0, wx0 + 7] x
+// [wy0, wy0 + 7] (offsets from the centre) is 0 if the centre lies inside,
+// else the least of its four edge minima (a clamped 1-D minimum each).  The
+// bound is widened (relative 2e-3, absolute 1e-3) so that no pixel the
+// compositing would take is ever skipped.
+__device__ __forceinline__ float edge_min_x(float a, float lo, float hi, float A, float B, float C) {
+  // min over dy in [lo, hi] of A a^2 + 2 B a dy + C dy^2
+  const float dy = fminf(fmaxf(-B * a / C, lo), hi);
+  return A * a * a + 2.f * B * a * dy + C * dy * dy;
 }
-
-// The alpha box of a splat at (x, y) reaches the warp's square.
-__device__ __forceinline__ bool box_hits(const WarpPix& q, float x, float y, float2 h) {
-  return h.x >= 0.f && !(x + h.x < q.wx0 || x - h.x > q.wx0 + 7.f || y + h.y < q.wy0 || y - h.y > q.wy0 + 7.f);
+__device__ __forceinline__ float edge_min_y(float b, float lo, float hi, float A, float B, float C) {
+  const float dx = fminf(fmaxf(-B * b / A, lo), hi);
+  return A * dx * dx + 2.f * B * dx * b + C * b * b;
+}
+__device__ __forceinline__ bool splat_hits(const WarpPix& q, float x, float y, float A, float B, float C, float o) {
+  const float L = logf(255.f * o);
+  if (!(L > 0.f)) return false;
+  const float ax0 = q.wx0 - x, ax1 = ax0 + 7.f, by0 = q.wy0 - y, by1 = by0 + 7.f;
+  if (ax0 <= 0.f && ax1 >= 0.f && by0 <= 0.f && by1 >= 0.f) return true;
+  float m = edge_min_x(ax0, by0, by1, A, B, C);
+  m = fminf(m, edge_min_x(ax1, by0, by1, A, B, C));
+  m = fminf(m, edge_min_y(by0, ax0, ax1, A, B, C));
+  m = fminf(m, edge_min_y(by1, ax0, ax1, A, B, C));
+  return m <= 2.004f * L + 1e-3f;
 }
 
 // One splat as staged in shared memory.
@@ -491,7 +502,7 @@ __device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, 
   slot->b = make_float4(co.z, co.w, cc.x, cc.y);
   slot->c = cc.z;
   slot->id = id;
-  return box_hits(q, g.x, g.y, alpha_box(co.x, co.y, co.z, co.w));
+  return splat_hits(q, g.x, g.y, co.x, co.y, co.z, co.w);
 }
 
 __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restrict__ ranges,
