@@ -942,6 +942,37 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
   pbwd_row<BF>(rl, c, ntiles, rgbv, conic_o, g2, V, grad, Vg, mode, item, lane, i, true);
 }
 
+// The chain rule of a whole batch in one pass over the listed rows: each row's
+// parameters are read once, the gradients of the cameras that see it are
+// summed in registers and stored once.
+template <bool BF>
+__global__ void __launch_bounds__(PP_THREADS, 2) k_preprocess_bwd_batch(RenderList rl, BatchGrad bg,
+                                                                    float* __restrict__ grad, uint64_t Vg,
+                                                                    const uint32_t* __restrict__ rows,
+                                                                    const uint32_t* __restrict__ nrows) {
+  const uint32_t B = rl.B;
+  const uint32_t n = *nrows;
+  for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
+    const uint32_t i = rows[t];
+    const unsigned item = i / B, lane = i - item * B;
+    const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
+    const float* p = rl.base + sbase;
+    const __nv_bfloat16* q16 = sh16(rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride, B, lane);
+    float g[D];
+#pragma unroll
+    for (int f = 0; f < D; ++f) g[f] = 0.f;
+    for (int j = 0; j < bg.J; ++j) {
+      if (bg.ntiles[j][i] == 0) continue;
+      float gv2[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gv2[q] = bg.g2[j][(uint64_t)q * bg.stride[j] + i];
+      chain_rule<BF>(bg.cam[j], p, q16, B, gv2, __float_as_uint(bg.rgb[j][i].w), bg.conic[j][i].w, g);
+    }
+#pragma unroll
+    for (int f = 0; f < D; ++f) grad[(uint64_t)f * Vg + i] = g[f];
+  }
+}
+
 // The render-list positions with touched != 0: one warp per 128 positions
 // (4 per lane), a warp scan of the counts and one atomic per warp, so each
 // group's rows are written in ascending order (groups in any order).
@@ -1461,6 +1492,28 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
   k_raster_bwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.g2_stride,
                                                    cs.order_valid ? cs.torder : nullptr);
+  TGS_LAUNCHED();
+}
+
+void render_backward_params_batch(const RenderList& rl, const DevCam* cams, CamState* const* cs, int J, float* grad,
+                                  const uint32_t* rows, const uint32_t* nrows, cudaStream_t s) {
+  if (rl.capacity() == 0 || J <= 0) return;
+  TGS_CHECK(J <= BatchGrad::MAXJ, TGS_ERR_INVALID, "batch larger than the fused chain rule supports");
+  BatchGrad bg;
+  bg.J = J;
+  for (int j = 0; j < J; ++j) {
+    bg.cam[j] = cams[j];
+    bg.ntiles[j] = cs[j]->ntiles;
+    bg.rgb[j] = cs[j]->rgb;
+    bg.conic[j] = cs[j]->conic_o;
+    bg.g2[j] = cs[j]->g2;
+    bg.stride[j] = cs[j]->g2_stride;
+  }
+  const unsigned grid = std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM);
+  if (rl.bf16)
+    k_preprocess_bwd_batch<true><<<grid, PP_THREADS, 0, s>>>(rl, bg, grad, rl.capacity(), rows, nrows);
+  else
+    k_preprocess_bwd_batch<false><<<grid, PP_THREADS, 0, s>>>(rl, bg, grad, rl.capacity(), rows, nrows);
   TGS_LAUNCHED();
 }
 

@@ -109,6 +109,21 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
 void render_backward_params(const RenderList& rl, const DevCam& cam, const CamState& cs, float* grad, int mode,
                             cudaStream_t s, const uint32_t* rows = nullptr, const uint32_t* nrows = nullptr);
 
+// The chain rule of a batch of J cameras in one pass over the listed rows
+// (their gradients summed in registers, stored once).
+struct BatchGrad {
+  static constexpr int MAXJ = 8;
+  int J = 0;
+  DevCam cam[MAXJ];
+  const uint32_t* ntiles[MAXJ];
+  const float4* rgb[MAXJ];
+  const float4* conic[MAXJ];
+  const float* g2[MAXJ];
+  uint64_t stride[MAXJ];
+};
+void render_backward_params_batch(const RenderList& rl, const DevCam* cams, CamState* const* cs, int J, float* grad,
+                                  const uint32_t* rows, const uint32_t* nrows, cudaStream_t s);
+
 // rows[0..*nrows) = the render-list positions with touched != 0 (groups of
 // 128 positions in ascending order, groups in any order).
 void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s);

@@ -726,15 +726,25 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     loss_norm[loss_enq % LOSS_RING] = (float)((uint64_t)J * pix * 3);
     ++loss_enq;
     timer.end(StageTimer::LOSS, comp);
+    std::vector<DevCam> dcs(J);
+    std::vector<CamState*> css(J);
     for (uint32_t j = 0; j < J; ++j) {
-      DevCam dc = make_devcam(p.cams[j]);
+      dcs[j] = make_devcam(p.cams[j]);
+      css[j] = &cams[j];
       timer.begin(StageTimer::BWD, comp);
-      render_backward_2d(rl, dc, cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
+      render_backward_2d(rl, dcs[j], cfg.bg, cams[j], dl_dimg + (uint64_t)j * pix * 3, comp);
       timer.end(StageTimer::BWD, comp);
-      timer.begin(StageTimer::PBWD, comp);
-      render_backward_params(rl, dc, cams[j], grad_local, j == 0 ? 0 : 1, comp, rows_dev, rows_dev + V_cap_rows);
-      timer.end(StageTimer::PBWD, comp);
     }
+    timer.begin(StageTimer::PBWD, comp);
+    if (J <= (uint32_t)BatchGrad::MAXJ) {
+      render_backward_params_batch(rl, dcs.data(), css.data(), (int)J, grad_local, rows_dev, rows_dev + V_cap_rows,
+                                   comp);
+    } else {
+      for (uint32_t j = 0; j < J; ++j)
+        render_backward_params(rl, dcs[j], cams[j], grad_local, j == 0 ? 0 : 1, comp, rows_dev,
+                               rows_dev + V_cap_rows);
+    }
+    timer.end(StageTimer::PBWD, comp);
     timer.begin(StageTimer::ADAM, comp);
     mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias);
     adam_render_list(rl, grad_local, rows_dev, rows_dev + V_cap_rows, item_bias, block_step, step_lrs(),

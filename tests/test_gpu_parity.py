@@ -247,3 +247,27 @@ def test_grouped_learning_rates_follow_the_schedule(orc, tgs):
     moved = step2 > 0
     assert moved.any() and step2[moved].max() <= 1e-5 * 1.5
     table.close()
+
+
+def test_two_camera_batch_matches_oracle(orc, tgs):
+    """A batch of two cameras (the fused chain rule sums both cameras'
+    gradients per Gaussian): loss, touched set, step counters and the summed
+    59-parameter gradient against the oracle."""
+    c, perm, Pm, cams, targets, table = _setup(orc, tgs, loss=1)
+    lval = table.step(c["cams"], np.stack(targets))
+    p_g, m1, _, st = table.state()
+    table.close()
+    K = 16
+    sph = orc.block_spheres(Pm.astype(np.float64), 1250)
+    _, vis = orc.visible_blocks(sph, cams)
+    P = Pm.astype(np.float64).copy()
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    steps = np.zeros(K, np.int64)
+    o = orc.train_step(P, M1, M2, steps, 1250, np.nonzero(vis)[0], cams, np.stack(targets), lr=1e-3, loss_kind=1)
+    assert abs(lval - o["loss"]) <= 1e-4 * o["loss"]
+    assert np.array_equal(st, steps.astype(np.uint32))
+    t = o["touched"].astype(bool)
+    g_gpu = m1[o["ids"]].astype(np.float64) / 0.1
+    assert rel_l2(g_gpu[t], o["grad"][t]) < 1e-3
+    for f in range(59):
+        assert rel_l2(g_gpu[t, f], o["grad"][t, f]) < 1e-3, f
