@@ -281,7 +281,7 @@ def run_street(args, rank, world, local):
     W, H = cams[0]["width"], cams[0]["height"]
     cache = int(args.cache_gb * 1e9 // (4096 * 708))
     base = dict(block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache, spare_slots=512,
-                moments_policy=0, loss=0)
+                moments_policy=0, loss=2)
     table = tgs.TideTable(host, prefetch_mode=0, **base)
     targets = torch.empty(nc, H, W, 3, device=dev, dtype=torch.float32)
     for i, c in enumerate(cams):
@@ -543,11 +543,11 @@ def cpu_baseline_street(res):
     M1, M2 = np.zeros_like(P), np.zeros_like(P)
     steps = np.zeros(len(sph), np.int64)
     t0 = time.perf_counter()
-    oracle.train_step(P, M1, M2, steps, B, blocks, [ca], target, lr=1e-3, loss_kind=0)
+    oracle.train_step(P, M1, M2, steps, B, blocks, [ca], target, lr=1e-3, loss_kind=2)
     dt = time.perf_counter() - t0
     return {"value": round(1.0 / dt, 6), "unit": "train iters/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"one step of camera 0: {len(sel)} Gaussians within {rad:.0f} m (the frustum's far corners), "
-                      f"{len(blocks)} visible blocks, 1600x900, FP64 forward+backward+Adam, {dt:.1f} s"}
+                      f"{len(blocks)} visible blocks, 1600x900, FP64 forward + L1/D-SSIM loss + backward + Adam, {dt:.1f} s"}
 
 
 # FP32 lane instructions per evaluated (pixel, splat) pair of the method's
@@ -559,24 +559,35 @@ RASTER_INSTR = {"raster_fwd": 22.0, "raster_bwd": 40.0}
 FP32_LANE_PEAK = 148 * 128 * 2.032e9
 
 
+def raster_source_sha():
+    """sha256 of the raster kernels' source: the part of raster.cu from the
+    raster CTA's comment up to the chain rule of the preprocess, followed by
+    common.cuh (the helpers they inline)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2605_20150_b300", "csrc")
+    text = open(os.path.join(csrc, "raster.cu"), "rb").read()
+    a = text.index(b"// Raster CTA: one 16x16 tile")
+    b = text.index(b"// Chain rule of the Level-2 preprocess")
+    return hashlib.sha256(text[a:b] + open(os.path.join(csrc, "common.cuh"), "rb").read()).hexdigest()
+
+
 def profiled_traffic(stage):
     """DRAM bytes per launch of the stage's kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
-    import hashlib
-    if stage != "raster_bwd":
+    summary, or None when the raster kernels' source changed since the
+    capture."""
+    if stage not in ("raster_fwd", "raster_bwd"):
         return None
     path = os.path.join(ROOT, "profiles", "raster_adam_street100m_cache2gb.md")
-    src = os.path.join(ROOT, "paper_2605_20150_b300", "csrc", "raster.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        sha = raster_source_sha()
+    except (OSError, ValueError):
         return None
     vals = {}
     for line in text.splitlines():
-        if line.startswith("- traffic_bytes_per_launch:"):
+        if line.startswith(f"- traffic_bytes_per_launch({stage}):"):
             vals["t"] = int(line.split(":")[1])
-        if line.startswith("- source_sha256("):
+        if line.startswith("- raster_source_sha256:"):
             vals["sha"] = line.split(":")[1].strip()
     return vals.get("t") if vals.get("sha") == sha else None
 
@@ -692,13 +703,13 @@ def reference_street(args):
     times = []
     for k in range(n_warm + n_steps):
         t1 = time.perf_counter()
-        oracle.train_step(P, M1, M2, steps, B, blocks, [ca], target, lr=1e-3, loss_kind=0)
+        oracle.train_step(P, M1, M2, steps, B, blocks, [ca], target, lr=1e-3, loss_kind=2)
         if k >= n_warm:
             times.append(time.perf_counter() - t1)
     v = len(times) / sum(times)
     cb = {"value": round(v, 6), "unit": "train iters/s", "cores": os.cpu_count(), "kind": "oracle",
           "sample": f"camera 0 of the street drive: {len(rows)} of {n} Gaussians within {rad:.0f} m "
-                    f"({len(blocks)} visible 4096-blocks), 1600x900, FP64 forward+backward+Adam, "
+                    f"({len(blocks)} visible 4096-blocks), 1600x900, FP64 forward + L1/D-SSIM loss + backward + Adam, "
                     f"{n_steps} steps of {1e3 * np.mean(times):.0f} ms; neighbourhood generated in {t_gen:.0f} s",
           "steps": n_steps, "warmup": n_warm}
     config = {"workload": "street-100M-1600x900-outofcore-bf16-learned", "n_gaussians": n, "block_size": B,
@@ -755,7 +766,7 @@ def run_city(args, rank, world, local):
     W, H = cams[0]["width"], cams[0]["height"]
     cache = int(160e9 * n / 1.1e9 // (4096 * 382))
     base = dict(block_size=4096, max_batch=J, max_width=W, max_height=H, cache_blocks=cache, spare_slots=1024,
-                moments_policy=0, loss=0, host_bf16=1, stochastic_round=1, prefetch_mode=1, max_render_blocks=6144)
+                moments_policy=0, loss=2, host_bf16=1, stochastic_round=1, prefetch_mode=1, max_render_blocks=6144)
     tb = tgs.TideTable(host, **base)
     nb = args.warmup + args.steps
     half = (nb + 1) // 2
@@ -864,6 +875,7 @@ def main():
                   "cameras": res["nc"], "heldout": "every 10th camera", "cache_blocks": res["cache_blocks"],
                   "cache_gb": args.cache_gb, "host_tier": "pinned: FP32 mean/scale/rot/opacity/SH-DC, BF16 SH-rest and moments",
                   "prefetch": "learned (MLP on the last 8 poses), exact culling for the actual batch",
+                  "loss": "(1 - 0.2) L1 + 0.2 (1 - SSIM), Adam lr 1e-3",
                   "parallelism": f"replicas{world}", "l2": "per-step state > 126 MB L2, no flush",
                   "setup_s": res["setup_s"]}
     elif city:

@@ -101,17 +101,6 @@ __device__ __forceinline__ KeyPath key_path(const DevCam& c, float mx, float my,
   return k;
 }
 
-// Exponent of a splat at pixel (px, py): -(A dx^2 + C dy^2)/2 - B dx dy, with
-// d = pixel - centre.  One definition, explicitly rounded, shared by the
-// forward and backward raster so both take identical skip/stop decisions.
-__device__ __forceinline__ float splat_power(float px, float py, float x, float y, float A, float B, float C,
-                                             float& dx, float& dy) {
-  dx = __fsub_rn(px, x);
-  dy = __fsub_rn(py, y);
-  float q = __fadd_rn(__fmul_rn(A, __fmul_rn(dx, dx)), __fmul_rn(C, __fmul_rn(dy, dy)));
-  return __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B, __fmul_rn(dx, dy)));
-}
-
 __device__ __forceinline__ float splat_alpha(float opac, float power, float& G) {
   G = __expf(power);
   return fminf(ALPHA_MAX, __fmul_rn(opac, G));

@@ -1004,10 +1004,8 @@ __global__ void k_touched_rows(const uint8_t* __restrict__ touched, uint64_t V, 
   }
 }
 
-constexpr int ADAM_FG = 8;     // fields per thread, FP32 record
-constexpr int ADAM_FG_BF = 4;  // fields per thread, BF16 record
+constexpr int ADAM_FG = 8;  // fields per thread
 constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
-constexpr int ADAM_GROUPS_BF = (D + ADAM_FG_BF - 1) / ADAM_FG_BF;
 
 template <bool BF>
 __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __restrict__ grad,
@@ -1049,8 +1047,8 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
       }
     }
   } else {
-    // BF16 record: two phases over ADAM_FG_BF fields (fewer than FP32 to keep
-    // the registers, and so the occupancy, up)
+    // BF16 record: field by field (a two-phase form costs occupancy here and
+    // measured slower)
     __nv_bfloat16* q16 = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
     __nv_bfloat16* m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
     __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
@@ -1059,34 +1057,25 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
     const uint32_t step = block_step[blk];
     const uint64_t gid = (uint64_t)blk * B + lane;
     const uint64_t key0 = ((uint64_t)rl.seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20);
-    float gf[ADAM_FG_BF], mf[ADAM_FG_BF], vf[ADAM_FG_BF], pf[ADAM_FG_BF];
 #pragma unroll
-    for (int q = 0; q < ADAM_FG_BF; ++q) {
+    for (int q = 0; q < ADAM_FG; ++q) {
       const int f = f0 + q;
       if (f < D) {
         const uint64_t o = (uint64_t)f * B;
-        gf[q] = grad[(uint64_t)f * V + i];
-        mf[q] = __bfloat162float(m[o]);
-        vf[q] = __bfloat162float(v[o]);
-        pf[q] = f < F_BF16 ? p[o] : __bfloat162float(q16[(uint64_t)(f - F_BF16) * B]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < ADAM_FG_BF; ++q) {
-      const int f = f0 + q;
-      if (f < D) {
-        const uint64_t o = (uint64_t)f * B;
-        const float mn = b1 * mf[q] + (1.f - b1) * gf[q];
-        const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
+        const float g = grad[(uint64_t)f * V + i];
+        const float mn = b1 * __bfloat162float(m[o]) + (1.f - b1) * g;
+        const float vn = b2 * __bfloat162float(v[o]) + (1.f - b2) * g * g;
         const float upd = lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
         // one counter hash per field: three 16-bit draws for m, v, parameter
         const uint64_t hsh = sr ? mix64(key0 + (uint64_t)f) : 0ull;
         m[o] = to_bf16(mn, sr, (uint32_t)hsh);
         v[o] = to_bf16(vn, sr, (uint32_t)(hsh >> 16));
-        if (f < F_BF16)
-          p[o] = pf[q] - upd;
-        else
-          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, (uint32_t)(hsh >> 32));
+        if (f < F_BF16) {
+          p[o] -= upd;
+        } else {
+          const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
+          q16[o16] = to_bf16(__bfloat162float(q16[o16]) - upd, sr, (uint32_t)(hsh >> 32));
+        }
       }
     }
   }
@@ -1107,7 +1096,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
                                                     const uint32_t* __restrict__ abort_flag) {
   if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
   const uint32_t B = rl.B, n = *nrows;
-  const int f0 = blockIdx.y * (BF ? ADAM_FG_BF : ADAM_FG);
+  const int f0 = blockIdx.y * ADAM_FG;
   for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
     const uint32_t i = rows[t];
     const unsigned item = i / B, lane = i - item * B;
@@ -1566,8 +1555,7 @@ void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* r
                       const float2* bias, const uint32_t* block_step, const LrSet& lr, float b1, float b2, float eps,
                       cudaStream_t s, const uint32_t* abort_flag) {
   if (rl.capacity() == 0) return;
-  const dim3 grid(std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM),
-                  rl.bf16 ? ADAM_GROUPS_BF : ADAM_GROUPS);
+  const dim3 grid(std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM), ADAM_GROUPS);
   if (rl.bf16)
     k_adam<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, rows, nrows, bias, block_step, rl.capacity(), lr, b1, b2, eps,
                                             abort_flag);

@@ -235,6 +235,8 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   }
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
+  free_fifo.clear();
+  for (uint64_t sl = 0; sl < n_slots; ++sl) free_fifo.push_back((uint32_t)sl);
   dirty_host.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
   wb_pending.assign(K, 0);
@@ -310,6 +312,8 @@ void Table::set_params(const float* params) {
   for (uint32_t* b : {r_bits, r_next_bits, acc_bits, acc_next_bits}) TGS_CUDA(cudaMemset(b, 0, words * sizeof(uint32_t)));
   slot_of.assign(K, -1);
   block_of_slot.assign(n_slots, -1);
+  free_fifo.clear();
+  for (uint64_t sl = 0; sl < n_slots; ++sl) free_fifo.push_back((uint32_t)sl);
   dirty_host.assign(n_slots, 0);
   slot_has_ev.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
@@ -498,12 +502,12 @@ void Table::prepare_finish(Prepared& out) {
   }
   r_host_prev = out.r_host;
 
-  // ---- slot assignment: free slots (ascending) for S+ in ascending id order,
-  // the rest into the slots that S- frees (ascending)
+  // ---- slot assignment: S+ in ascending id order takes the free slots that
+  // have been free the longest (a FIFO: their last write-back and reads are
+  // long done, so an early copy never waits behind them on the copy stream),
+  // the rest take the slots S- frees (ascending); S- slots not reused join
+  // the back of the FIFO.
   CopyPlan& pl = out.plan;
-  std::vector<uint32_t> free_slots;
-  for (uint64_t s = 0; s < n_slots; ++s)
-    if (block_of_slot[s] < 0) free_slots.push_back((uint32_t)s);
   std::vector<uint32_t> ev_slots;
   for (uint32_t b : out.s_minus) {
     TGS_CHECK(slot_of[b] >= 0, TGS_ERR_STATE, "evicted block is not resident");
@@ -512,17 +516,19 @@ void Table::prepare_finish(Prepared& out) {
     pl.evict_slot.push_back((uint32_t)slot_of[b]);
   }
   std::sort(ev_slots.begin(), ev_slots.end());
-  size_t fi = 0, ei = 0;
+  size_t ei = 0;
   for (uint32_t b : out.s_plus) {
-    if (fi < free_slots.size()) {
+    if (!free_fifo.empty()) {
       pl.early_block.push_back(b);
-      pl.early_slot.push_back(free_slots[fi++]);
+      pl.early_slot.push_back(free_fifo.front());
+      free_fifo.pop_front();
     } else {
       TGS_CHECK(ei < ev_slots.size(), TGS_ERR_CAPACITY, "no slot left for an incoming block");
       pl.late_block.push_back(b);
       pl.late_slot.push_back(ev_slots[ei++]);
     }
   }
+  for (; ei < ev_slots.size(); ++ei) free_fifo.push_back(ev_slots[ei]);
   if (!cfg.differential) {
     // a block may leave and come back in the same selection: every load goes
     // after the write-backs (late), so a reload sees its written-back record

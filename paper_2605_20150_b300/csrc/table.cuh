@@ -99,6 +99,7 @@ struct Table {
   std::vector<uint8_t> slot_has_ev;
   std::vector<uint8_t> ever_loaded;      // K: for the re-admission counter
   std::vector<uint8_t> wb_pending;       // K: write-back to the host tier issued, not yet waited on
+  std::deque<uint32_t> free_fifo;        // free slots, longest free first
   cudaEvent_t ev_wb = nullptr;           // recorded after each write-back batch on d2h
   cudaEvent_t ev_snap = nullptr;         // recorded after the bounds snapshot on comp
 
