@@ -742,7 +742,7 @@ def host_mem_available():
 
 
 def run_city(args, rank, world, local):
-    """The mixed city configuration (config 4's shape): street grid with roof
+    """The mixed city configuration: street grid with roof
     detail over 16 km^2, SH-rest and Adam moments BF16 in pinned host memory,
     2,000 cameras at 1920x1080 (an aerial lawnmower pass at 150 m, pitch 45
     degrees, then two street drives), batch 4, exact next-batch prefetch.  The

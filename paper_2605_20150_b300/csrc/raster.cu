@@ -353,15 +353,63 @@ __global__ void __launch_bounds__(EP_THREADS) k_emit_pairs(const uint32_t* __res
   }
 }
 
+// List segments of the backward work split.  A tile whose list is longer
+// than R_SEG is composited backward as ceil(length / R_SEG) segments (at most
+// R_NSEG_MAX, the last one taking the rest), each an independent CTA; the
+// forward records per pixel (T, accumulated colour) at every segment boundary
+// and, in one more slot, (T_final, final colour).  One tile's backward is
+// otherwise a single CTA whose serial work can exceed the share of an SM slot
+// several times (the longest lists are a few percent of the tiles).
+constexpr int R_SEG = 256;  // a multiple of 32 (one staging batch)
+constexpr uint32_t R_NSEG_MAX = 255;
+__host__ __device__ __forceinline__ uint32_t seg_count(uint32_t len) {
+  const uint32_t n = (len + R_SEG - 1) / R_SEG;
+  return n <= 1 ? 1u : (n < R_NSEG_MAX ? n : R_NSEG_MAX);
+}
+
 // Tile order of the raster launches, longest pair list first (so the long
 // tiles do not start last), in one CTA: a stable counting sort of the tiles on
 // a logarithmic length bucket (255 - 16 log2(1 + length), clamped to 0..255);
-// the order is a scheduling heuristic, so bucket ties keep tile order.
+// the order is a scheduling heuristic, so bucket ties keep tile order.  Then,
+// in that order, the checkpoint slots of the split tiles (while they fit in
+// ck_cap) and the backward units (tile | segment << 24), their count in
+// *n_units.
 constexpr int TO_THREADS = 1024;
+__device__ __forceinline__ uint32_t to_block_scan(uint32_t x, uint32_t* sw, uint32_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sw[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = sw[lane];  // TO_THREADS / 32 == 32 warps
+    uint32_t vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    sw[lane] = vi - v;
+    if (lane == 31) sw[32] = vi;
+  }
+  __syncthreads();
+  const uint32_t r = sw[w] + inc - x;
+  total = sw[32];
+  __syncthreads();
+  return r;
+}
+
 __global__ void __launch_bounds__(TO_THREADS) k_tile_order(const uint2* __restrict__ ranges, uint32_t tiles,
-                                                          uint32_t* __restrict__ order) {
+                                                          uint32_t* __restrict__ order, uint32_t* __restrict__ tck,
+                                                          uint32_t* __restrict__ units,
+                                                          uint32_t* __restrict__ n_units, uint32_t ck_cap) {
   __shared__ uint32_t cnt[32][256];
   __shared__ uint32_t base[256];
+  __shared__ uint32_t sw[33];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int e = tid; e < 32 * 256; e += TO_THREADS) (&cnt[0][0])[e] = 0;
   __syncthreads();
@@ -412,6 +460,32 @@ __global__ void __launch_bounds__(TO_THREADS) k_tile_order(const uint2* __restri
     if (ok) order[base[b] + o + __popc(peers & lt)] = t;
     __syncwarp();
   }
+  if (!units) return;
+  __syncthreads();  // order[] is read back below by other threads of the CTA
+  uint32_t ccarry = 0, ucarry = 0;
+  for (uint32_t i0 = 0; i0 < tiles; i0 += TO_THREADS) {
+    const uint32_t i = i0 + tid;
+    uint32_t t = 0, ns = 1;
+    if (i < tiles) {
+      t = order[i];
+      const uint2 r = ranges[t];
+      ns = seg_count(r.y - r.x);
+    }
+    // a split tile takes ns slots: ns - 1 boundaries and its final state
+    const uint32_t want = ns > 1 ? ns : 0u;
+    uint32_t ctot, utot;
+    const uint32_t cb = ccarry + to_block_scan(want, sw, ctot);
+    const bool split = want > 0 && cb + want <= ck_cap;
+    const uint32_t nu = split ? ns : 1u;
+    const uint32_t ub = ucarry + to_block_scan(nu, sw, utot);
+    if (i < tiles) {
+      tck[t] = split ? cb : ~0u;
+      for (uint32_t g = 0; g < nu; ++g) units[ub + g] = t | (g << 24);
+    }
+    ccarry += ctot;
+    ucarry += utot;
+  }
+  if (tid == 0) *n_units = ucarry;
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, const uint32_t* __restrict__ pkeys,
@@ -512,7 +586,9 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
                                                          const float4* __restrict__ rgb, int W, int H, int TX,
                                                          float3 bg, float* __restrict__ img,
                                                          float* __restrict__ t_final, int* __restrict__ n_last,
-                                                         const uint32_t* __restrict__ order) {
+                                                         const uint32_t* __restrict__ order,
+                                                         const uint32_t* __restrict__ tck,
+                                                         float4* __restrict__ ck) {
   __shared__ Splat s_sp[R_WARPS][32];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const WarpPix q = warp_pixels(tile, TX);
@@ -520,6 +596,10 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
   Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
   const int n = (int)(r.y - r.x);
+  // checkpoints of a split tile (the backward work split): slot ck0 + i - 1
+  // holds the state before list position i R_SEG, slot ck0 + ns - 1 the final
+  const uint32_t ck0 = tck ? tck[tile] : ~0u;
+  const int ns = (int)seg_count((uint32_t)n);
   const float fpx = (float)q.px;
   float T[R_PPT], C0[R_PPT], C1[R_PPT], C2[R_PPT];
   int last[R_PPT];
@@ -535,6 +615,11 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
   }
   bool going = __any_sync(0xffffffffu, act);
   for (int b = 0; b < n && going; b += 32) {
+    if (ck0 != ~0u && b > 0 && b % R_SEG == 0 && b / R_SEG < ns) {
+      float4* c = ck + (uint64_t)(ck0 + b / R_SEG - 1) * TILE_PIX + threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < R_PPT; ++k) c[k * R_THREADS] = make_float4(T[k], C0[k], C1[k], C2[k]);
+    }
     const bool hit = b + lane < n && stage_splat(pvals, xy, conic_o, rgb, r.x + b + lane, q, &sp[lane]);
     __syncwarp();
     uint32_t bal = __ballot_sync(0xffffffffu, hit);
@@ -576,6 +661,11 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
     }
     __syncwarp();  // the batch slots are rewritten next
   }
+  if (ck0 != ~0u) {
+    float4* c = ck + (uint64_t)(ck0 + ns - 1) * TILE_PIX + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < R_PPT; ++k) c[k * R_THREADS] = make_float4(T[k], C0[k], C1[k], C2[k]);
+  }
 #pragma unroll
   for (int k = 0; k < R_PPT; ++k) {
     const int py = q.py0 + k;
@@ -604,14 +694,31 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
                                                          float3 bg, const float* __restrict__ t_final,
                                                          const int* __restrict__ n_last,
                                                          const float* __restrict__ dl_dimg, float* __restrict__ g2,
-                                                         uint64_t V, const uint32_t* __restrict__ order) {
+                                                         uint64_t V, const uint32_t* __restrict__ units,
+                                                         const uint32_t* __restrict__ n_units,
+                                                         const uint32_t* __restrict__ tck,
+                                                         const float4* __restrict__ ck) {
   __shared__ Splat s_sp[R_WARPS][32];
-  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+  // the CTA's unit: one tile, or one list segment [b0, b1) of a split tile
+  int tile = (int)blockIdx.x, seg = 0;
+  if (units) {
+    if (blockIdx.x >= *n_units) return;  // uniform per CTA
+    const uint32_t u = units[blockIdx.x];
+    tile = (int)(u & 0xFFFFFFu);
+    seg = (int)(u >> 24);
+  }
   const WarpPix q = warp_pixels(tile, TX);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
   const float fpx = (float)q.px;
+  const uint32_t ck0 = units ? tck[tile] : ~0u;
+  const int ns = (int)seg_count(r.y - r.x);
+  int b0 = 0, b1 = 0x7fffffff;
+  if (ck0 != ~0u) {
+    b0 = seg * R_SEG;
+    if (seg + 1 < ns) b1 = (seg + 1) * R_SEG;
+  }
   // Qs = sum_c dL/dC_c S_c, S_c the colour composited behind the current
   // splat (only this combination enters dL/dalpha)
   float T[R_PPT], gr[R_PPT], gg[R_PPT], gb[R_PPT], Qs[R_PPT], tfb[R_PPT];
@@ -639,6 +746,20 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
   int wlast = mylast;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+  if (wlast <= b0) return;  // nothing of this segment reaches the warp's pixels (no CTA barrier follows)
+  if (wlast > b1) {
+    // the segment lies below the warp's last contribution: start from the
+    // forward's state at b1, T = T(b1) and S_c = (C_c final - C_c(b1)) / T(b1)
+    const float4* cf = ck + (uint64_t)(ck0 + ns - 1) * TILE_PIX + threadIdx.x;
+    const float4* c1 = ck + (uint64_t)(ck0 + seg) * TILE_PIX + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < R_PPT; ++k) {
+      const float4 f = cf[k * R_THREADS], a = c1[k * R_THREADS];
+      T[k] = a.x;
+      Qs[k] = (gr[k] * (f.y - a.y) + gg[k] * (f.z - a.z) + gb[k] * (f.w - a.w)) / a.x;
+    }
+    wlast = b1;
+  }
   // reduce-scatter roles: lane l ends with the warp sum of value
   // 4 bit4(l) + 2 bit3(l) + bit2(l) of v[0..7]; v[8] by butterfly
   const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
@@ -647,10 +768,10 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
   // (sum 0: A sx + B sy; sum 1: B sx + C sy; conic sums: -1/2, -1, -1/2)
   const float cA = qsel == 0 ? 1.f : 0.f, cC = qsel == 1 ? 1.f : 0.f, cB = qsel < 2 ? 1.f : 0.f;
   const float cK = qsel < 2 ? 0.f : (qsel == 3 ? -1.f : (qsel == 2 || qsel == 4 ? -0.5f : 1.f));
-  for (int top = wlast; top > 0; top -= 32) {
+  for (int top = wlast; top > b0; top -= 32) {
     // lane l stages list position top - 1 - l: ascending lanes, descending positions
     const int k0 = top - 1 - lane;
-    const bool hit = k0 >= 0 && stage_splat(pvals, xy, conic_o, rgb, r.x + (uint32_t)k0, q, &sp[lane]);
+    const bool hit = k0 >= b0 && stage_splat(pvals, xy, conic_o, rgb, r.x + (uint32_t)k0, q, &sp[lane]);
     __syncwarp();
     uint32_t bal = __ballot_sync(0xffffffffu, hit);
     while (bal) {
@@ -1294,8 +1415,13 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.n_last, cs.cap_pix * sizeof(int)));
   TGS_CUDA(cudaMalloc(&cs.counters, 8 * sizeof(uint32_t)));
   TGS_CUDA(cudaMallocHost(&cs.counters_host, 4 * sizeof(uint32_t)));
-  TGS_CUDA(cudaMalloc(&cs.tkeys, 2 * cs.cap_tiles * sizeof(uint32_t)));
   TGS_CUDA(cudaMalloc(&cs.torder, 2 * cs.cap_tiles * sizeof(uint32_t)));
+  // backward split: up to 4 checkpoint slots per tile, at most 8192 (32 MB)
+  TGS_CHECK(cs.cap_tiles < (1ull << 24), TGS_ERR_INVALID, "image has too many tiles");
+  cs.ck_cap = (uint32_t)std::min<uint64_t>(8192, 4 * cs.cap_tiles);
+  TGS_CUDA(cudaMalloc(&cs.ck, (uint64_t)cs.ck_cap * TILE_PIX * sizeof(float4)));
+  TGS_CUDA(cudaMalloc(&cs.tck, cs.cap_tiles * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.units, (cs.cap_tiles + cs.ck_cap) * sizeof(uint32_t)));
   TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_counts, cudaEventDisableTiming));
   TGS_CUDA(cudaMemset(cs.counters, 0, 8 * sizeof(uint32_t)));
   cs.cap_pairs = 0;
@@ -1330,7 +1456,7 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
 void cam_state_free(CamState& cs) {
   void* ptrs[] = {cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.dkeys,
                   cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch,
-                  cs.tkeys, cs.torder};
+                  cs.torder, cs.ck, cs.tck, cs.units};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (cs.counters_host) cudaFreeHost(cs.counters_host);
@@ -1384,7 +1510,8 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
                          bits_for(tiles), cs.scratch, s, cs.hint_np);
     k_ranges<<<2 * NSM, 256, 0, s>>>(np_dev, cs.cap_pairs, cs.pkeys, cs.ranges);
     TGS_LAUNCHED();
-    k_tile_order<<<1, TO_THREADS, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.torder);
+    k_tile_order<<<1, TO_THREADS, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.torder, cs.tck, cs.units,
+                                          cs.counters + 5, cs.ck_cap);
     TGS_LAUNCHED();
     cs.order_valid = true;
     tm->end(StageTimer::SORT, s);
@@ -1394,7 +1521,8 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   tm->begin(StageTimer::FWD, s);
   k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last,
-                                                   cs.order_valid ? cs.torder : nullptr);
+                                                   cs.order_valid ? cs.torder : nullptr,
+                                                   cs.order_valid ? cs.tck : nullptr, cs.ck);
   TGS_LAUNCHED();
   tm->end(StageTimer::FWD, s);
   // the counts reach the host asynchronously (read by cam_state_counts)
@@ -1475,7 +1603,8 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
     }
   }
   k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, image, cs.t_final, cs.n_last, nullptr);
+                                                   cam.TX, bg3, image, cs.t_final, cs.n_last, nullptr, nullptr,
+                                                   nullptr);
   cs.order_valid = false;
   TGS_LAUNCHED();
 }
@@ -1490,9 +1619,15 @@ void render_backward_2d(const RenderList& rl, const DevCam& cam, const float bg[
   cs.g2_stride = V;
   TGS_CUDA(cudaMemsetAsync(cs.g2, 0, 9 * V * sizeof(float), s));
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
-  k_raster_bwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
-                                                   cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.g2_stride,
-                                                   cs.order_valid ? cs.torder : nullptr);
+  // with a valid tile order: one CTA per backward unit (longest lists
+  // first, long lists split into segments); the unit count stays on the
+  // device, so the grid takes its bound and the surplus CTAs return at once
+  const bool split = cs.order_valid;
+  const uint64_t grid = split ? tiles + cs.ck_cap : tiles;
+  k_raster_bwd<<<(unsigned)grid, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+                                                  cam.TX, bg3, cs.t_final, cs.n_last, dl_dimage, cs.g2, cs.g2_stride,
+                                                  split ? cs.units : nullptr, cs.counters + 5,
+                                                  split ? cs.tck : nullptr, cs.ck);
   TGS_LAUNCHED();
 }
 

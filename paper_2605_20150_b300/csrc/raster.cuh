@@ -55,15 +55,22 @@ struct CamState {
   uint32_t* pvals = nullptr;
   // per tile / pixel
   uint2* ranges = nullptr;
-  uint32_t* tkeys = nullptr;   // 2 x cap_tiles: tile-order sort keys (ping-pong)
   uint32_t* torder = nullptr;  // 2 x cap_tiles: tiles, longest pair list first
   bool order_valid = false;
+  // backward work split: a tile with a long list is composited backward as
+  // several independent list segments, each started from the forward's
+  // per-pixel state (T, accumulated colour) at its upper boundary
+  uint32_t ck_cap = 0;         // checkpoint slots (TILE_PIX float4 each)
+  float4* ck = nullptr;        // ck_cap x TILE_PIX
+  uint32_t* tck = nullptr;     // cap_tiles: first checkpoint slot of a split tile, ~0u otherwise
+  uint32_t* units = nullptr;   // cap_tiles + ck_cap: backward units, tile | segment << 24
   float* t_final = nullptr;
   int* n_last = nullptr;
   // scratch for scans and sorts
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  uint32_t* counters = nullptr;  // device [8]: n_vis, n_pairs (before the clamp), overflow, pairs needed, tiles
+  uint32_t* counters = nullptr;  // device [8]: n_vis, n_pairs (before the clamp), overflow, pairs needed, -,
+                                 // backward units
   uint32_t* counters_host = nullptr;  // pinned mirror, copied at the end of each render
   cudaEvent_t ev_counts = nullptr;    // recorded after that copy
   uint32_t* step_flag = nullptr;      // optional device word raised with the overflow flag

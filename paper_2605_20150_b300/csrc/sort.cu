@@ -377,8 +377,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rsd_hist(const uint32_t* __restr
 // One CTA: exclusive scan of the digit-major count table counts[d][c] in
 // place, which gives the global start of (digit d, chunk c).  Each thread
 // scans a contiguous segment (independent loads, cached lines), the segment
-// sums are scanned across the block.
+// sums are scanned across the block.  Used up to RSO_MAX entries (96 per
+// thread); one launch there is cheaper than the chunked three-kernel scan.
 constexpr int RSO_THREADS = 1024;
+constexpr uint64_t RSO_MAX = 96ull * RSO_THREADS;
 __global__ void __launch_bounds__(RSO_THREADS) k_rsd_offsets(uint32_t* __restrict__ counts, uint32_t G) {
   __shared__ uint32_t sw[RSO_THREADS / 32 + 1];
   const uint32_t E = RS_BINS * G;
@@ -543,7 +545,7 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
     uint32_t mask = (1u << nb) - 1u;
     k_radix_hist<<<nc, RS_THREADS, 0, s>>>(ki, n, shift, mask, counts, nc);
     TGS_LAUNCHED();
-    if ((uint64_t)nc * RS_BINS <= 4 * RSO_THREADS) {
+    if ((uint64_t)nc * RS_BINS <= RSO_MAX) {
       k_rsd_offsets<<<1, RSO_THREADS, 0, s>>>(counts, nc);  // same digit-major table
       TGS_LAUNCHED();
     } else {
@@ -610,7 +612,7 @@ void radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, ui
     uint32_t mask = (1u << nb) - 1u;
     k_rsd_hist<<<G, RS_THREADS, 0, s>>>(ki, n_dev, cap, shift, mask, counts);
     TGS_LAUNCHED();
-    if (E <= 4 * RSO_THREADS) {
+    if (E <= RSO_MAX) {
       k_rsd_offsets<<<1, RSO_THREADS, 0, s>>>(counts, G);
       TGS_LAUNCHED();
     } else {

@@ -122,6 +122,19 @@ def test_step_matches_oracle(orc, tgs, loss):
     _check_step(orc, tgs, c["params"], 1250, c["cams"][0], targets[0], loss, 256, 256)
 
 
+def test_step_dssim_ragged_image(orc, tgs):
+    """L1 + D-SSIM at 200 x 150: neither side is a multiple of the 16-pixel
+    raster tiles or of the 32-pixel tiles of the SSIM filters, so the halo
+    and the image edges cut through tiles."""
+    cfg = scenes.small_cube_config()
+    R, t = scenes.look_at([0.0, 0.0, -3.0], [0.7, 0.7, -0.7])
+    camd = scenes.pinhole(200, 150, 22.0, R, t)
+    tp = scenes.perturb(cfg["params"], seed=79)
+    _, Pt = orc.create(tp, 250)
+    target = orc.render(Pt.astype(np.float64), scenes.camera_array(camd))["img"].astype(np.float32)
+    _check_step(orc, tgs, cfg["params"], 250, camd, target, 2, 200, 150)
+
+
 def test_step_partial_render_list(orc, tgs):
     """A camera that sees about half of 80 blocks: the render list is a strict
     subset of the cache capacity (the layout of the per-step arrays differs
