@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(TO_THREADS) k_tile_order(const uint2* __restri
     uint32_t ctot, utot;
     const uint32_t cb = ccarry + to_block_scan(want, sw, ctot);
     const bool split = want > 0 && cb + want <= ck_cap;
-    const uint32_t nu = split ? ns : 1u;
+    const uint32_t nu = i < tiles ? (split ? ns : 1u) : 0u;
     const uint32_t ub = ucarry + to_block_scan(nu, sw, utot);
     if (i < tiles) {
       tck[t] = split ? cb : ~0u;
