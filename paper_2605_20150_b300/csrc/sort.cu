@@ -377,10 +377,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rsd_hist(const uint32_t* __restr
 // One CTA: exclusive scan of the digit-major count table counts[d][c] in
 // place, which gives the global start of (digit d, chunk c).  Each thread
 // scans a contiguous segment (independent loads, cached lines), the segment
-// sums are scanned across the block.  Used up to RSO_MAX entries (96 per
-// thread); one launch there is cheaper than the chunked three-kernel scan.
+// sums are scanned across the block.  Used up to RSO_MAX entries (4 per
+// thread): with longer segments the serial loads of one CTA cost more than
+// the chunked scan (measured 32 us for 18k-76k entries).
 constexpr int RSO_THREADS = 1024;
-constexpr uint64_t RSO_MAX = 96ull * RSO_THREADS;
+constexpr uint64_t RSO_MAX = 4ull * RSO_THREADS;
 __global__ void __launch_bounds__(RSO_THREADS) k_rsd_offsets(uint32_t* __restrict__ counts, uint32_t G) {
   __shared__ uint32_t sw[RSO_THREADS / 32 + 1];
   const uint32_t E = RS_BINS * G;

@@ -10,7 +10,10 @@ from parity_util import image_within, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,B,size", [(20000, 1250, 256), (3001, 512, 200)])
+# 256: long tile lists split into backward segments, all 256 tiles in one
+# 1,024-tile chunk of the tile order; 200: ragged edge tiles; 640: 1,600
+# tiles (two chunks of the order and of the backward units), 376 split
+@pytest.mark.parametrize("n,B,size", [(20000, 1250, 256), (3001, 512, 200), (20000, 1250, 640)])
 def test_autograd_matches_oracle(orc, tgs, n, B, size):
     import torch
     cfg = scenes.small_cube_config(n=n, size=size)
