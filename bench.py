@@ -62,6 +62,31 @@ def dist_env():
     return rank, world, local
 
 
+def rank_barrier(world):
+    """All replicas enter (or leave) a timed region together."""
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x, world):
+    """The largest of a per-rank value (the slowest replica's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_iters_per_s(world, ms_per_step):
+    """Whole-job throughput of `world` replicas that each ran one step per
+    ms_per_step (the maximum over ranks): weak scaling, no shared work."""
+    return world * 1e3 / ms_per_step
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -159,8 +184,7 @@ def run_ours(args, rank, world, local):
         one(t)
     table.sync()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    rank_barrier(world)
     launches0 = table.stats()["kernel_launches"]
     table.stage_timing(True)
     table.stage_ms(reset=True)
@@ -182,10 +206,8 @@ def run_ours(args, rank, world, local):
     st = table.stats()
     launches = st["kernel_launches"] - launches0
     rec = table.camera_record(0, W, H)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    rank_barrier(world)
+    ms = max_over_ranks(ms, world)
     # ---- end to end through the C ABI with host buffers: targets from pinned
     # host memory copied inside every step, every step's loss copied back
     # (read with tgs_losses at the end of the timed region)
@@ -318,6 +340,7 @@ def run_street(args, rank, world, local):
         clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        rank_barrier(world)
         torch.cuda.nvtx.range_push("timed:" + label)
         e0.record(s)
         for k in range(args.warmup, args.warmup + args.steps):
@@ -326,8 +349,9 @@ def run_street(args, rank, world, local):
         torch.cuda.nvtx.range_pop()
         tab.sync()
         torch.cuda.synchronize()
+        rank_barrier(world)
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
         stages = tab.stage_ms(reset=True)
         tab.stage_timing(False)
         st = tab.stats()
@@ -803,6 +827,7 @@ def run_city(args, rank, world, local):
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    rank_barrier(world)
     torch.cuda.nvtx.range_push("timed:city")
     e0.record(s)
     for b in range(args.warmup, nb):
@@ -811,8 +836,9 @@ def run_city(args, rank, world, local):
     torch.cuda.nvtx.range_pop()
     tb.sync()
     torch.cuda.synchronize()
+    rank_barrier(world)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     stages = tb.stage_ms(reset=True)
     tb.stage_timing(False)
     st = tb.stats()
@@ -868,7 +894,8 @@ def main():
     else:
         res = run_street(args, rank, world, local) if street else run_ours(args, rank, world, local)
     ms_step = res["ms"] / args.steps
-    value = world * 1e3 / ms_step
+    value = job_iters_per_s(world, ms_step)
+    e2e_ms = max_over_ranks(res["e2e_ms"], world)
     if street:
         config = {"workload": "street-100M-1600x900-outofcore-bf16-learned", "n_gaussians": res["n"],
                   "block_size": 4096, "image": f"{res['W']}x{res['H']}", "global_batch": world,
@@ -894,7 +921,7 @@ def main():
         "metric": METRIC, "value": round(value, 3), "unit": "train iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
-        "e2e": {"value": round(world * 1e3 / res["e2e_ms"], 3), "unit": "train iters/s",
+        "e2e": {"value": round(job_iters_per_s(world, e2e_ms), 3), "unit": "train iters/s",
                 "h2d_bytes_per_step": res["bytes_in"], "d2h_bytes_per_step": 4},
         "gpu_launches": int(res["launches"]),
         "roofline": roofline(res, args.steps),
