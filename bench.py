@@ -221,6 +221,8 @@ def run_ours(args, rank, world, local):
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     table.losses()
+    torch.cuda.synchronize()
+    rank_barrier(world)
     e2.record(s)
     t0 = time.perf_counter()
     for t in range(n_e2e):
@@ -228,6 +230,7 @@ def run_ours(args, rank, world, local):
     e2e_losses = table.losses()
     e3.record(s)
     torch.cuda.synchronize()
+    rank_barrier(world)
     assert len(e2e_losses) == n_e2e and np.isfinite(e2e_losses).all()
     wall_e2e = time.perf_counter() - t0
     e2e_ms = max(e2.elapsed_time(e3), 1e3 * wall_e2e) / n_e2e
@@ -405,6 +408,7 @@ def run_street(args, rank, world, local):
         tb.step([cams[k]], host_np[k:k + 1], next_cams=[cams[k + 1]], want_loss=False)
     tb.losses()
     torch.cuda.synchronize()
+    rank_barrier(world)
     t1 = time.perf_counter()
     for k in range(w_e2e, w_e2e + n_e2e):
         i = k % host_np.shape[0]
@@ -413,6 +417,7 @@ def run_street(args, rank, world, local):
     e2e_losses = tb.losses()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
+    rank_barrier(world)
     assert len(e2e_losses) == n_e2e and np.isfinite(e2e_losses).all()
     d = head["delta"]
     link = {"peak_gbs": peak, "bytes_h2d_per_step": d["bytes_h2d"] / args.steps,
@@ -862,6 +867,7 @@ def run_city(args, rank, world, local):
     n_e2e = 4
     tb.losses()
     torch.cuda.synchronize()
+    rank_barrier(world)
     t1 = time.perf_counter()
     for b in range(n_e2e):
         ids = batches[b]
@@ -870,6 +876,7 @@ def run_city(args, rank, world, local):
     assert len(tb.losses()) == n_e2e
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t1) / n_e2e
+    rank_barrier(world)
     return dict(ms=ms, stages=stages, stats=st, launches=d["kernel_launches"], clocks=clocks, rec=rec, table=tb,
                 e2e_ms=e2e_ms, bytes_in=J * H * W * 3 * 4, link=link, n=n, nc=nc, W=W, H=H, cache_blocks=cache,
                 setup_s=round(t_setup, 1), bf16=True, host_avail_gb=round(avail / 1e9, 1))
