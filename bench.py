@@ -457,10 +457,13 @@ def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=40, warm=5)
     prefetch as the full method): the same n steps with differential streaming
     off (every selection evicts the cache and streams the selected set again),
     with copy/compute overlap off, and with blocks in input order instead of
-    Morton order."""
+    Morton order; and the paper's Shuffle scheduling variant (Sec. 4.2, the
+    in-memory overhead runs; App. A.2, the ordering ablation): the full method
+    with the training cameras visited in a seeded random order instead of the
+    trajectory order."""
     import torch
     variants = [("full", {}), ("no_differential", {"differential": 0}), ("no_overlap", {"overlap": 0}),
-                ("no_morton", {"morton": 0})]
+                ("no_morton", {"morton": 0}), ("shuffle", {})]
     res = {}
     for name, kw in variants:
         cfg = dict(base)
@@ -471,7 +474,7 @@ def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=40, warm=5)
             # more blocks than the cache holds at the street setting
             cfg["cache_blocks"] = int(cfg["cache_blocks"])
         t = tgs.TideTable(host, **cfg)
-        seq = train_ids
+        seq = np.random.default_rng(1005).permutation(train_ids) if name == "shuffle" else train_ids
 
         def one(k):
             i, j = seq[k % len(seq)], seq[(k + 1) % len(seq)]
