@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cache-gb", type=float, default=24.0, help="HBM working-set cache cap (street workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ablation", action="store_true",
-                    help="street: also time the Tab. 5 ablations (no differential streaming, no overlap, no Morton)")
+                    help="street: also time the Tab. 5 ablations (no differential streaming, no overlap, no Morton) and the Shuffle camera order")
     return ap.parse_args()
 
 
