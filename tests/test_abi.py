@@ -50,3 +50,27 @@ def test_struct_layouts_match_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe], text=True).split()]
     assert sizes == [ctypes.sizeof(m.tgs_camera), ctypes.sizeof(m.tgs_config), ctypes.sizeof(m.tgs_stats)]
+
+
+def test_struct_field_offsets_match_header():
+    """Every field of the ctypes mirrors sits at the C offset of the field of
+    the same name (a reordered or mistyped field would corrupt configs
+    silently)."""
+    import tempfile
+    import paper_2605_20150_b300 as m
+    structs = [("tgs_camera", m.tgs_camera), ("tgs_config", m.tgs_config), ("tgs_stats", m.tgs_stats)]
+    lines, want = [], []
+    for cname, py in structs:
+        for name, _ in py._fields_:
+            # Python keywords carry a trailing underscore in the mirror (lambda_)
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {name.rstrip("_")}));')
+            want.append(getattr(py, name).offset)
+    src = '#include "tidegs.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){' + "".join(lines) + "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        with open(c, "w") as f:
+            f.write(src)
+        exe = os.path.join(d, "p")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe], text=True).split()]
+    assert got == want
