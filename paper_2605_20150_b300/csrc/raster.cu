@@ -503,12 +503,13 @@ __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, cons
 // pixel square and each thread two vertically adjacent pixels of it.  The
 // warps are independent: each walks the tile's list 32 splats at a time,
 // lane l staging splat l of the batch in the warp's slice of shared memory
-// together with the test of its alpha box (outside which alpha < 1/255)
-// against the warp's square; a ballot of that test is the warp's work list,
-// taken in list order, so results are those of visiting every splat.  Pixels
-// are evaluated with predicated, branch-free updates; a warp stops when its
+// together with the test of its alpha >= 1/255 ellipse against the warp's
+// square (splat_hits); a ballot of that test is the warp's work list, taken
+// in list order, so results are those of visiting every splat.  Pixels are
+// evaluated with predicated, branch-free updates; a warp stops when its
 // pixels are saturated (forward) and starts at the largest n_last of its
-// pixels (backward), without waiting for the other warps.
+// pixels (backward), without waiting for the other warps.  A backward CTA
+// takes one unit: a whole tile, or one list segment of a split tile.
 constexpr int R_PPT = 2;
 constexpr int R_THREADS = TILE_PIX / R_PPT;  // 128
 constexpr int R_WARPS = R_THREADS / 32;
