@@ -87,22 +87,57 @@ def job_iters_per_s(world, ms_per_step):
     return world * 1e3 / ms_per_step
 
 
-class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+
+def clock_summary(lines, t0=None, t1=None):
+    """Median SM clock, maximum clock and active throttle reasons of nvidia-smi
+    CSV lines (timestamp, index, clocks.sm, clocks.max.sm, power, active
+    mask, then the four reasons), over the samples taken inside the wall-clock
+    window [t0, t1] when there are any, else over all samples (warm-up and
+    timed region; `window` says which)."""
+    import datetime
+    rows = []
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            sm, mx = float(f[2]), float(f[3])
+        except ValueError:
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        rows.append((ts, sm, mx, [v.lower() == "active" for v in f[6:10]]))
+    inside = [r for r in rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
+    use = inside if inside else rows
+    reasons = sorted({nm for r in use for nm, on in zip(REASONS, r[3]) if on})
+    return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+            "sm_max_mhz": max(r[2] for r in use) if use else None, "reasons": reasons, "samples": len(use),
+            "window": "timed" if inside else "warm-up and timed"}
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons,
+    started before the warm-up so that it runs through the timed region;
+    mark() brackets the timed region in wall-clock time."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -113,6 +148,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, end=False):
+        if end:
+            self.t1 = time.time()
+        else:
+            self.t0 = time.time()
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -121,22 +162,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return clock_summary(list(self.lines), self.t0, self.t1 if self.t1 is not None else time.time())
 
 
 def measured_peaks():
@@ -180,6 +206,8 @@ def run_ours(args, rank, world, local):
         return table.step([cams[t % nc]], targets[t % nc:t % nc + 1], next_cams=[cams[(t + 1) % nc]],
                           want_loss=want_loss)
 
+    clk = ClockSampler(local)
+    clk.start()
     for t in range(args.warmup):
         one(t)
     table.sync()
@@ -188,17 +216,17 @@ def run_ours(args, rank, world, local):
     launches0 = table.stats()["kernel_launches"]
     table.stage_timing(True)
     table.stage_ms(reset=True)
-    clk = ClockSampler(local)
-    clk.start()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    clk.mark()
     e0.record(s)
     for t in range(args.warmup, args.warmup + args.steps):
         one(t)
     e1.record(s)
     table.sync()
     torch.cuda.synchronize()
+    clk.mark(end=True)
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     stages = table.stage_ms(reset=True)
@@ -333,17 +361,18 @@ def run_street(args, rank, world, local):
             j = seq[(k + 1) % len(seq)]
             tab.step([cams[i]], targets[i:i + 1], next_cams=[cams[j]], want_loss=False)
 
+        clk = ClockSampler(local)
+        clk.start()
         for k in range(args.warmup):
             one(k)
         tab.sync()
         st0 = tab.stats()
         tab.stage_timing(True)
         tab.stage_ms(reset=True)
-        clk = ClockSampler(local)
-        clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         rank_barrier(world)
+        clk.mark()
         torch.cuda.nvtx.range_push("timed:" + label)
         e0.record(s)
         for k in range(args.warmup, args.warmup + args.steps):
@@ -352,6 +381,7 @@ def run_street(args, rank, world, local):
         torch.cuda.nvtx.range_pop()
         tab.sync()
         torch.cuda.synchronize()
+        clk.mark(end=True)
         rank_barrier(world)
         clocks = clk.stop()
         ms = max_over_ranks(e0.elapsed_time(e1), world)
@@ -825,17 +855,18 @@ def run_city(args, rank, world, local):
         tb.step([cams[i] for i in ids], targets[k0:k0 + J], next_cams=[cams[i] for i in nxt] if nxt else None,
                 want_loss=False)
 
+    clk = ClockSampler(local)
+    clk.start()
     for b in range(args.warmup):
         one(b)
     tb.sync()
     st0 = tb.stats()
     tb.stage_timing(True)
     tb.stage_ms(reset=True)
-    clk = ClockSampler(local)
-    clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     rank_barrier(world)
+    clk.mark()
     torch.cuda.nvtx.range_push("timed:city")
     e0.record(s)
     for b in range(args.warmup, nb):
@@ -844,6 +875,7 @@ def run_city(args, rank, world, local):
     torch.cuda.nvtx.range_pop()
     tb.sync()
     torch.cuda.synchronize()
+    clk.mark(end=True)
     rank_barrier(world)
     clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
