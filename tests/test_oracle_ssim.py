@@ -117,3 +117,18 @@ def test_structure_term_closed_form():
         cxy = k * vx
         want = (2 * mx * my + 1e-4) * (2 * cxy + 9e-4) / ((mx * mx + my * my + 1e-4) * (vx + vy + 9e-4))
         np.testing.assert_allclose(t["S"][i, j], want, rtol=1e-10)
+
+
+def test_batch_is_the_mean_of_its_images():
+    """A batch of J same-size images: the loss is the mean of the per-image
+    losses and each image's gradient is its own gradient divided by J (no
+    window crosses from one image into the next)."""
+    from oracle import ssim
+    rng = np.random.default_rng(5)
+    xs, ys = zip(*[_imgs(rng, 10, 12) for _ in range(3)])
+    X, Y = np.stack(xs), np.stack(ys)
+    per = [ssim.loss(x, y) for x, y in zip(xs, ys)]
+    assert abs(ssim.loss(X, Y) - np.mean(per)) < 1e-14
+    G = ssim.loss_grad(X, Y)
+    for j, (x, y) in enumerate(zip(xs, ys)):
+        np.testing.assert_allclose(G[j], ssim.loss_grad(x, y) / 3.0, rtol=1e-12, atol=1e-18)
