@@ -141,6 +141,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # nvidia-smi takes a moment to start: wait (at most 2 s) for its
+            # first sample so that short timed regions are covered
+            t_end = time.time() + 2.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
 
@@ -633,11 +638,11 @@ def raster_source_sha():
     return hashlib.sha256(text[a:b] + open(os.path.join(csrc, "common.cuh"), "rb").read()).hexdigest()
 
 
-def profiled_traffic(stage):
+def profiled_traffic(stage, workload="street100m"):
     """DRAM bytes per launch of the stage's kernel from the committed ncu
-    summary, or None when the raster kernels' source changed since the
-    capture."""
-    if stage not in ("raster_fwd", "raster_bwd"):
+    summary of the street workload, or None for another workload or when the
+    raster kernels' source changed since the capture."""
+    if stage not in ("raster_fwd", "raster_bwd") or workload != "street100m":
         return None
     path = os.path.join(ROOT, "profiles", "raster_adam_street100m_cache2gb.md")
     try:
@@ -654,7 +659,7 @@ def profiled_traffic(stage):
     return vals.get("t") if vals.get("sha") == sha else None
 
 
-def roofline(res, steps):
+def roofline(res, steps, workload="street100m"):
     """Roofline of the dominant stage.  Raster: FP32 ALU bound, achieved =
     evaluated pairs (sum of n_last over pixels) x instructions per pair / time
     against the FP32 lane peak.  Adam: HBM bound, 1,652 B (FP32 record) or
@@ -670,7 +675,7 @@ def roofline(res, steps):
         evals = float(res["rec"]["n_last"].astype(np.float64).sum())
         ach = evals * RASTER_INSTR[name] / (ms_per * 1e-3)
         out.update(bound="alu", achieved=round(ach / 1e12, 3), peak=round(FP32_LANE_PEAK / 1e12, 2),
-                   unit="T FP32 lane-instr/s", frac=round(ach / FP32_LANE_PEAK, 4), traffic=profiled_traffic(name),
+                   unit="T FP32 lane-instr/s", frac=round(ach / FP32_LANE_PEAK, 4), traffic=profiled_traffic(name, workload),
                    evals_per_launch=evals, instr_per_eval=RASTER_INSTR[name],
                    peak_source="derived: 148 SMs x 128 FP32 lanes x 2.032 GHz")
     elif name == "adam":
@@ -966,7 +971,7 @@ def main():
         "e2e": {"value": round(job_iters_per_s(world, e2e_ms), 3), "unit": "train iters/s",
                 "h2d_bytes_per_step": res["bytes_in"], "d2h_bytes_per_step": 4},
         "gpu_launches": int(res["launches"]),
-        "roofline": roofline(res, args.steps),
+        "roofline": roofline(res, args.steps, args.workload),
         "clocks": res["clocks"],
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["stages"].items()},
         "visible": res["stats"]["last_visible"], "pairs": res["stats"]["last_pairs"],
