@@ -233,3 +233,108 @@ def test_clamp_and_dilation_radius(orc):
     np.testing.assert_allclose(S[0, 23], s2 + math.sqrt(0.1), rtol=1e-14)
     np.testing.assert_allclose(S[0, orc.CA], 1 / s2, rtol=1e-14)
     np.testing.assert_allclose(S[0, orc.CB], 0.0, atol=1e-18)
+
+
+# ----------------------------------------------------------------------------
+# Anisotropic, rotated and off-axis projection (standard EWA splatting, the
+# Level-2 preprocess of Sec. 3.3): pinned against scipy's rotations and a
+# finite-difference linearisation of the pinhole map, so that a transposed
+# rotation, a conjugated quaternion or a swapped off-diagonal term fails.
+# ----------------------------------------------------------------------------
+def _conic_to_cov(S, i):
+    """2D covariance (dilated) of splat i from the oracle's conic (A, B, C):
+    the conic is its inverse, [[A, B], [B, C]] = cov^-1."""
+    A, B, C = S[i, 3], S[i, 4], S[i, 5]
+    return np.linalg.inv(np.array([[A, B], [B, C]]))
+
+
+def _sigma_scipy(quat_wxyz, scales):
+    """World covariance R diag(s^2) R^T with R from scipy (scalar-last order)."""
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = quat_wxyz
+    Rq = Rotation.from_quat([x, y, z, w]).as_matrix()
+    return Rq @ np.diag(np.asarray(scales) ** 2) @ Rq.T
+
+
+def test_quarter_turn_about_z_swaps_the_2d_variances(orc):
+    """q = (cos 45, 0, 0, sin 45) maps x to y: an on-axis Gaussian with scales
+    (s1, s2, s3) projects to diag((f s2/z)^2 + 0.3, (f s1/z)^2 + 0.3) exactly
+    (the camera looks down +z, no skew term)."""
+    f, z0 = 70.0, 2.5
+    cam = _axis_camera(64, 64, f)
+    s1, s2, s3 = 0.011, 0.047, 0.02
+    p = np.zeros((1, 59))
+    p[0, 2] = z0
+    p[0, 3:6] = np.log([s1, s2, s3])
+    p[0, 6:10] = [math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4)]
+    S = orc.preprocess(p, cam, fp32key=False)
+    assert S[0, orc.VISIBLE] == 1
+    a = (f * s2 / z0) ** 2 + 0.3
+    c = (f * s1 / z0) ** 2 + 0.3
+    np.testing.assert_allclose(S[0, orc.CA], 1.0 / a, rtol=1e-12)
+    np.testing.assert_allclose(S[0, orc.CC], 1.0 / c, rtol=1e-12)
+    assert abs(S[0, orc.CB]) < 1e-12 * S[0, orc.CA]
+    # lambda1 = the larger variance (mid^2 - det = ((a - c)/2)^2 > 0.1 here)
+    np.testing.assert_allclose(S[0, 23], max(a, c), rtol=1e-12)
+
+
+def test_rotation_matches_scipy_on_axis(orc):
+    """On the optical axis of an identity camera the Jacobian is diag(f/z, f/z)
+    in its first two columns and zero in the third, so the 2D covariance is
+    (f/z)^2 times the top-left 2x2 block of the world covariance plus 0.3 I;
+    the world covariance comes from scipy's rotation of random (unnormalised)
+    quaternions with anisotropic scales."""
+    rng = np.random.default_rng(31)
+    f, z0 = 90.0, 3.0
+    cam = _axis_camera(96, 96, f)
+    n = 64
+    p = np.zeros((n, 59))
+    p[:, 2] = z0
+    scales = np.exp(rng.uniform(np.log(0.005), np.log(0.05), size=(n, 3)))
+    p[:, 3:6] = np.log(scales)
+    p[:, 6:10] = rng.normal(size=(n, 4)) * 2.7
+    S = orc.preprocess(p, cam, fp32key=False)
+    for i in range(n):
+        Sig = _sigma_scipy(p[i, 6:10], scales[i])
+        expect = (f / z0) ** 2 * Sig[:2, :2] + 0.3 * np.eye(2)
+        np.testing.assert_allclose(_conic_to_cov(S, i), expect, rtol=1e-10, atol=1e-12)
+
+
+def test_off_axis_projection_matches_finite_difference_linearisation(orc):
+    """EWA projects the world covariance through the linearisation of the
+    pinhole map at the mean: cov2D = J Sigma J^T + 0.3 I with J = d(u, v)/d(mu).
+    Here J is taken by central differences of the projection itself (not the
+    analytic formula), for random camera poses, rotations and anisotropic
+    scales with the mean well inside the Jacobian's clamp limits."""
+    rng = np.random.default_rng(32)
+    W = H = 128
+    for trial in range(24):
+        pos = rng.normal(size=3) * 2.0
+        tgt = rng.normal(size=3) * 0.3
+        R, t = scenes.look_at(pos, tgt, up=tuple(rng.normal(size=3)))
+        camd = scenes.pinhole(W, H, 65.0, R, t)
+        cam = scenes.camera_array(camd)
+        fx, fy, cx, cy = camd["fx"], camd["fy"], camd["cx"], camd["cy"]
+        # a mean in view: camera coordinates (x, y, z) with |x/z|, |y/z| < 0.5
+        zc = rng.uniform(1.0, 4.0)
+        xc, yc = rng.uniform(-0.5, 0.5, size=2) * zc
+        mu = R.T @ (np.array([xc, yc, zc]) - t)
+        scales = np.exp(rng.uniform(np.log(0.004), np.log(0.04), size=3))
+        q = rng.normal(size=4)
+        p = np.zeros((1, 59))
+        p[0, 0:3] = mu
+        p[0, 3:6] = np.log(scales)
+        p[0, 6:10] = q
+        S = orc.preprocess(p, cam, fp32key=False)
+        assert S[0, orc.VISIBLE] == 1
+
+        def proj(m):
+            c = R @ m + t
+            return np.array([fx * c[0] / c[2] + cx, fy * c[1] / c[2] + cy])
+
+        h = 1e-5
+        Jfd = np.stack([(proj(mu + h * e) - proj(mu - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        expect = Jfd @ _sigma_scipy(q, scales) @ Jfd.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(_conic_to_cov(S, 0), expect, rtol=1e-7, atol=1e-9)
+        # the projected centre is the pinhole map of the mean
+        np.testing.assert_allclose([S[0, orc.U], S[0, orc.V]], proj(mu), rtol=0, atol=1e-9)
