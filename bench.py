@@ -114,9 +114,12 @@ def clock_summary(lines, t0=None, t1=None):
     inside = [r for r in rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
     use = inside if inside else rows
     reasons = sorted({nm for r in use for nm, on in zip(REASONS, r[3]) if on})
-    return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
-            "sm_max_mhz": max(r[2] for r in use) if use else None, "reasons": reasons, "samples": len(use),
-            "window": "timed" if inside else "warm-up and timed"}
+    out = {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+           "sm_max_mhz": max(r[2] for r in use) if use else None, "reasons": reasons, "samples": len(use),
+           "window": "timed" if inside else "warm-up and timed"}
+    if len(use) < 10:
+        out["weak"] = "fewer than 10 samples"
+    return out
 
 
 class ClockSampler:
@@ -128,8 +131,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, cuda_ordinal):
+        # nvidia-smi numbers GPUs its own way and ignores CUDA_VISIBLE_DEVICES:
+        # name the device by its UUID, which both sides agree on
+        self.gpu = gpu_smi_id(cuda_ordinal)
         self.proc = None
         self.lines = []
         self.t0 = self.t1 = None
@@ -168,6 +173,16 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         return clock_summary(list(self.lines), self.t0, self.t1 if self.t1 is not None else time.time())
+
+
+def gpu_smi_id(cuda_ordinal):
+    """nvidia-smi's --id for a CUDA device ordinal of this process: GPU-<uuid>."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(cuda_ordinal).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # no CUDA device: the sampler reports nvidia-smi unavailable
+        return str(cuda_ordinal)
 
 
 def measured_peaks():

@@ -353,18 +353,19 @@ tgs_status tgs_raster_backward(tgs_raster* r, const float* params_dev, uint64_t 
                                float* grad_dev, uint8_t* touched_dev, void* stream);
 
 /* Forward render like tgs_raster_forward for callers that cannot allocate
- * device memory when they render (inside a CUDA stream capture, where
- * cudaMalloc is not allowed; under a fixed memory budget owned by another
- * allocator; in loops that must not allocate).  The paper has no counterpart.
+ * device memory when they render (under a fixed memory budget owned by another
+ * allocator, where an allocation of their own would fail or fragment it; in
+ * real-time loops that must not allocate).  The paper has no counterpart.
  * All intermediates live in one 16 MiB file-scope device array that every GPU
  * loading the library holds until exit; nothing is allocated per call.
  * Limits: ceil(n / block_size) * block_size <= 32768, width * height <=
  * 512 * 512 (at most 1024 tiles), at most 524288 (tile, Gaussian) pairs;
  * beyond them the call returns TGS_ERR_CAPACITY and renders nothing.
  * The first call on a device looks the array up (cudaGetSymbolAddress) with
- * that device current: make it before any stream capture.  Calls share the
- * array and keep its last contents; calls whose GPU work overlaps race.  The
- * call returns when its work on `stream` has completed.
+ * that device current: make it before any stream capture.  The call reads
+ * the visible and pair counts back to the host (it waits on `stream`) and
+ * returns when its work on `stream` has completed.  Calls share the array
+ * and keep its last contents; calls whose GPU work overlaps race.
  * params_dev, image_dev, bg3: as for tgs_raster_forward. */
 tgs_status tgs_raster_forward_noalloc(const float* params_dev, uint64_t n, uint32_t block_size,
                                       const tgs_camera* cam, const float* bg3, float* image_dev, void* stream);

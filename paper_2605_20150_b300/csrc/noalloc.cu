@@ -1,10 +1,10 @@
 // Forward rasteriser that allocates nothing (tgs_raster_forward_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they render:
-// code running while a CUDA stream is being captured into a graph (where
-// cudaMalloc is not allowed), renderers that run inside a fixed, pre-reserved
-// memory budget owned by another framework's allocator, or real-time loops
-// that must not pay for an allocation.  For them this entry point keeps every
+// renderers that run inside a fixed, pre-reserved memory budget owned by
+// another framework's allocator (a cudaMalloc of their own would fail or
+// fragment that budget), or real-time loops that must not pay for an
+// allocation or risk one failing mid-frame.  For them this entry point keeps every
 // intermediate of the forward (per-Gaussian splats, visibility compaction,
 // the depth and tile radix sorts, the pair lists, tile ranges and per-pixel
 // state) in one file-scope device array of fixed size, g_noalloc_scratch.
@@ -14,7 +14,9 @@
 // the name is only a stand-in for the device object.  The first call on each
 // device resolves the array's device address with cudaGetSymbolAddress (with
 // that device current) and caches it; make that first call before any stream
-// capture begins.  All calls share the one array, which keeps the previous
+// capture begins.  The call reads the visible and pair counts back to the host
+// (it waits on `stream` twice) and returns after its work has completed.  All
+// calls share the one array, which keeps the previous
 // call's contents: what must start at zero (the tile ranges) is cleared by
 // each call, and two calls whose GPU work overlaps (different streams, or
 // different host threads) race on the array.

@@ -37,3 +37,17 @@ def test_reasons_and_fallback_to_all_samples():
     s = bench.clock_summary(lines, t - 1.0, t + 1.0)
     assert s["window"] == "timed" and s["reasons"] == ["sw_power_cap"]
     assert bench.clock_summary([], 0.0, 1.0)["sm_mhz"] is None
+
+
+def test_sampler_names_the_gpu_by_uuid_and_flags_thin_windows():
+    """nvidia-smi ignores CUDA_VISIBLE_DEVICES, so the sampler names its GPU by
+    UUID; a summary over fewer than 10 samples says so."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sid = bench.gpu_smi_id(0)
+    assert sid.startswith("GPU-") or sid == "0"  # "0" only without a CUDA device
+    t = 1_800_000_000.0
+    s = bench.clock_summary([_line(t + 0.01 * i, 2032, 2032) for i in range(3)], t - 1, t + 1)
+    assert s["samples"] == 3 and "weak" in s
+    s = bench.clock_summary([_line(t + 0.01 * i, 2032, 2032) for i in range(12)], t - 1, t + 1)
+    assert s["samples"] == 12 and "weak" not in s

@@ -1,8 +1,8 @@
 """The allocation-free forward renderer, tgs_raster_forward_noalloc.
 
-Callers that cannot allocate device memory when they render -- code running
-under a CUDA stream capture, renderers confined to a memory budget owned by
-another allocator, loops that must not allocate -- use this entry point; it
+Callers that cannot allocate device memory when they render -- renderers
+confined to a memory budget owned by another allocator, real-time loops that
+must not allocate -- use this entry point; it
 keeps its intermediates in a fixed static device array instead of buffers from
 cudaMalloc.  This test calls it through the C ABI twice in a row and checks
 each image against the regular entry point, tgs_raster_forward, within the
@@ -54,3 +54,30 @@ def test_noalloc_rejects_oversize_inputs(tgs):
     with pytest.raises(tgs.TgsError) as e:
         tgs.raster_forward_noalloc(big, 50000, cfg["cams"][0], (0, 0, 0), out)
     assert e.value.code == 4
+
+
+def test_noalloc_rejects_too_many_pairs(tgs):
+    """Within the Gaussian and image limits, a render whose (tile, Gaussian)
+    pairs exceed the fixed 524,288 is rejected before any pair is written: the
+    count comes from the scan of per-Gaussian tile counts, checked on the host
+    ahead of pair emission."""
+    import torch
+    cfg = scenes.small_cube_config(n=1250, size=512)
+    p = torch.tensor(cfg["params"], device="cuda")
+    # 1,250 Gaussians around the origin with scales of the cube's size: each
+    # covers most of the 32 x 32 tiles of a 512 x 512 view at distance 3
+    p[:, 0:3] *= 0.05
+    p[:, 3:6] = float(np.log(0.6))
+    p[:, 10] = 3.0
+    blocks = tgs.to_block_layout(p, 1250)
+    out = torch.zeros(512, 512, 3, device="cuda")
+    with pytest.raises(tgs.TgsError) as e:
+        tgs.raster_forward_noalloc(blocks, 1250, cfg["cams"][0], (0, 0, 0), out)
+    assert e.value.code == 4
+    assert "pairs" in str(e.value)
+    # the table is still usable afterwards: a small render succeeds
+    cfg2, blocks2 = _inputs(torch, tgs)
+    ok = torch.zeros(256, 256, 3, device="cuda")
+    tgs.raster_forward_noalloc(blocks2, 20000, cfg2["cams"][0], (0, 0, 0), ok)
+    torch.cuda.synchronize()
+    assert ok.abs().sum().item() > 0
