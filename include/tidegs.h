@@ -116,6 +116,17 @@ typedef struct tgs_config {
    * Overlap". */
   uint32_t differential;
   uint32_t morton;
+  /* Host second tier (Sec. 3.4, "CPU tiered cache" over storage):
+   * host_cache_blocks = 0 (or >= the block count) keeps every block record in
+   * pinned host memory; otherwise the records live in an append-only log file
+   * at backing_path (created or replaced; removed with the table) and a pool
+   * of host_cache_blocks pinned record slots caches them (LRU): a block
+   * streamed to the GPU is read from the log on a pool miss, a dirty block
+   * written back from the GPU stays in the pool and is appended to the log
+   * when the pool recycles its slot.  backing_path: borrowed during
+   * tgs_create / tgs_resume (copied). */
+  uint64_t host_cache_blocks;
+  const char* backing_path;
 } tgs_config;
 
 void tgs_default_config(tgs_config* cfg);
@@ -216,6 +227,14 @@ tgs_status tgs_get_params(tgs_table* t, float* out_host);
  * step counters (K values, may be NULL). */
 tgs_status tgs_get_state(tgs_table* t, float* params_host, float* m1_host, float* m2_host, uint32_t* steps_host);
 
+/* The same barrier, then selected rows of that state: ids (host, count
+ * block-order ids, any order, repeats allowed); params / m1 / m2 (host,
+ * count x 59 each, any may be NULL) receive those rows in the order of ids.
+ * For checking a table of 10^8 Gaussians without reading all of it.
+ * Errors: TGS_ERR_INVALID (an id >= n). */
+tgs_status tgs_get_state_rows(tgs_table* t, const int64_t* ids, uint64_t count, float* params_host, float* m1_host,
+                              float* m2_host);
+
 /* perm_host[g] = original row of the Gaussian with block-order id g (n values). */
 tgs_status tgs_get_block_order(tgs_table* t, int64_t* perm_host);
 
@@ -268,6 +287,19 @@ typedef struct tgs_stats {
   /* Host time inside tgs_step, and of it the time blocked on the control
    * stream's selections (Algorithm 1 lists read back). */
   double host_step_ms, host_wait_ms;
+  /* Residency churn (App. A.4, Tab. 9): resident_block_steps = sum over
+   * training steps of the resident blocks |R_t|; block_updates = blocks with
+   * an updated Gaussian, summed over steps; cold_updates = of those, the
+   * first update of a block after a re-admission (the update that starts
+   * from zeroed moments under moments_policy 1; counted under either
+   * policy, the residency decisions do not depend on it); streaks /
+   * streak_steps = completed residencies (a
+   * block's stay from admission to eviction) and their total length in
+   * steps. */
+  uint64_t resident_block_steps, block_updates, cold_updates, streaks, streak_steps;
+  /* Host second tier (host_cache_blocks > 0): pool hits and misses of block
+   * accesses, bytes read from and appended to the log. */
+  uint64_t host_cache_hits, host_cache_misses, log_bytes_read, log_bytes_written;
 } tgs_stats;
 tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out);
 

@@ -43,7 +43,8 @@ class tgs_config(ctypes.Structure):
                 ("host_bf16", ctypes.c_uint32), ("stochastic_round", ctypes.c_uint32), ("seed", ctypes.c_uint32),
                 ("pair_capacity", ctypes.c_uint64), ("max_render_blocks", ctypes.c_uint64),
                 ("lr_schedule", ctypes.c_uint32), ("lr_groups", ctypes.c_float * 6), ("lr_means_final", ctypes.c_float),
-                ("lr_decay_steps", ctypes.c_uint32), ("differential", ctypes.c_uint32), ("morton", ctypes.c_uint32)]
+                ("lr_decay_steps", ctypes.c_uint32), ("differential", ctypes.c_uint32), ("morton", ctypes.c_uint32),
+                ("host_cache_blocks", ctypes.c_uint64), ("backing_path", ctypes.c_char_p)]
 
 
 class tgs_stats(ctypes.Structure):
@@ -55,7 +56,11 @@ class tgs_stats(ctypes.Structure):
                 ("predicted_blocks", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_visible", ctypes.c_uint64), ("last_render_blocks", ctypes.c_uint64),
                 ("pair_overflows", ctypes.c_uint64), ("dropped_steps", ctypes.c_uint64),
-                ("host_step_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double)]
+                ("host_step_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double),
+                ("resident_block_steps", ctypes.c_uint64), ("block_updates", ctypes.c_uint64),
+                ("cold_updates", ctypes.c_uint64), ("streaks", ctypes.c_uint64), ("streak_steps", ctypes.c_uint64),
+                ("host_cache_hits", ctypes.c_uint64), ("host_cache_misses", ctypes.c_uint64),
+                ("log_bytes_read", ctypes.c_uint64), ("log_bytes_written", ctypes.c_uint64)]
 
 
 _VP = ctypes.c_void_p
@@ -77,6 +82,7 @@ _SIGS = {
     "tgs_get_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_set_params": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_state": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP]),
+    "tgs_get_state_rows": (ctypes.c_int32, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "tgs_get_block_order": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_spheres": (ctypes.c_int32, [_VP, _VP]),
     "tgs_get_sizes": (ctypes.c_int32, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
@@ -179,6 +185,8 @@ def default_config(**kw) -> tgs_config:
                 c.lr_groups[i] = v[i]
         elif k == "lam":
             c.lambda_ = v
+        elif k == "backing_path":
+            c.backing_path = None if v is None else os.fsencode(v)
         else:
             setattr(c, k, v)
     return c
@@ -273,6 +281,13 @@ class TideTable:
         st = np.zeros(self.K, np.uint32)
         _check(load().tgs_get_state(self.h, _ptr(p), _ptr(m), _ptr(v), _ptr(st)))
         return p, m, v, st
+
+    def state_rows(self, ids):
+        """(params, m1, m2) rows of the given block-order ids (tgs_get_state_rows)."""
+        ids = np.ascontiguousarray(ids, np.int64)
+        p, m, v = (np.zeros((len(ids), D), np.float32) for _ in range(3))
+        _check(load().tgs_get_state_rows(self.h, _ptr(ids), len(ids), _ptr(p), _ptr(m), _ptr(v)))
+        return p, m, v
 
     def block_order(self):
         out = np.zeros(self.n, np.int64)

@@ -220,7 +220,7 @@ tgs_status tgs_set_schedule(tgs_table* t, const tgs_camera* cams, uint64_t n, ui
 tgs_status tgs_sync(tgs_table* t) {
   return guard([&] {
     TGS_CHECK(t, TGS_ERR_INVALID, "tgs_sync: null table");
-    for (cudaStream_t s : {t->t.comp, t->t.h2d, t->t.d2h, t->t.ctl}) TGS_CUDA(cudaStreamSynchronize(s));
+    for (cudaStream_t s : {t->t.comp, t->t.h2d, t->t.h2d_late, t->t.tgtq, t->t.d2h, t->t.ctl}) TGS_CUDA(cudaStreamSynchronize(s));
     t->t.collect_stall();
     t->t.check_overflow(true);
   });
@@ -242,9 +242,14 @@ static void read_state(Table& T, float* params, float* m1, float* m2, bool origi
     if (bf) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[(uint64_t)f * B + l]);
     return base[(uint64_t)f * B + l];
   };
+  const float* rec = nullptr;
+  uint64_t rec_k = ~0ull;
   for (uint64_t g = 0; g < T.N; ++g) {
     uint64_t k = g / B, l = g % B;
-    const float* rec = T.host + k * rf;
+    if (k != rec_k) {
+      rec = T.tier.acquire_read((uint32_t)k);
+      rec_k = k;
+    }
     uint64_t row = original_order ? T.perm[g] : g;
     if (params)
       for (int f = 0; f < D; ++f)
@@ -260,6 +265,61 @@ static void read_state(Table& T, float* params, float* m1, float* m2, bool origi
       for (int f = 0; f < D; ++f) dst[row * D + f] = mrec ? moment(mrec, q, f, l) : 0.f;
     }
   }
+}
+
+// Rows ids[0..count) (block-order ids) of the state after the consistency
+// barrier; under cold restart the moments of a resident block come from its
+// HBM slot (one record copy per distinct resident block), of others are 0.
+static void read_state_rows(Table& T, const int64_t* ids, uint64_t count, float* params, float* m1, float* m2) {
+  T.flush();
+  const uint64_t B = T.B, rf = T.rec_floats;
+  const bool bf = T.cfg.host_bf16 != 0;
+  std::vector<float> slotrec;
+  int64_t slot_blk = -1;
+  auto field = [&](const float* rec, int f, uint64_t l) -> float {
+    if (bf && f >= F_BF16)
+      return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rec + (uint64_t)F_BF16 * B)[(uint64_t)(f - F_BF16) * B + l]);
+    return rec[(uint64_t)f * B + l];
+  };
+  auto moment = [&](const float* rec, int q, int f, uint64_t l) -> float {
+    const float* base = rec + T.p_floats + (uint64_t)q * T.m_floats;
+    if (bf) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[(uint64_t)f * B + l]);
+    return base[(uint64_t)f * B + l];
+  };
+  for (uint64_t r = 0; r < count; ++r) {
+    TGS_CHECK(ids[r] >= 0 && (uint64_t)ids[r] < T.N, TGS_ERR_INVALID, "tgs_get_state_rows: id out of range");
+    const uint64_t g = (uint64_t)ids[r], k = g / B, l = g % B;
+    const float* rec = T.tier.acquire_read((uint32_t)k);
+    if (params)
+      for (int f = 0; f < D; ++f) params[r * D + f] = field(rec, f, l);
+    if (!m1 && !m2) continue;
+    const float* mrec = rec;
+    if (T.cfg.moments_policy == 1) {
+      mrec = nullptr;
+      if (T.slot_of[k] >= 0) {
+        if (slot_blk != (int64_t)k) {
+          slotrec.resize(rf);
+          TGS_CUDA(cudaMemcpy(slotrec.data(), T.pool + (uint64_t)T.slot_of[k] * rf, rf * sizeof(float),
+                              cudaMemcpyDeviceToHost));
+          slot_blk = (int64_t)k;
+        }
+        mrec = slotrec.data();
+      }
+    }
+    for (int q = 0; q < 2; ++q) {
+      float* dst = q == 0 ? m1 : m2;
+      if (!dst) continue;
+      for (int f = 0; f < D; ++f) dst[r * D + f] = mrec ? moment(mrec, q, f, l) : 0.f;
+    }
+  }
+}
+
+tgs_status tgs_get_state_rows(tgs_table* t, const int64_t* ids, uint64_t count, float* params_host, float* m1_host,
+                              float* m2_host) {
+  return guard([&] {
+    TGS_CHECK(t && (ids || count == 0), TGS_ERR_INVALID, "tgs_get_state_rows: null argument");
+    read_state_rows(t->t, ids, count, params_host, m1_host, m2_host);
+  });
 }
 
 tgs_status tgs_set_params(tgs_table* t, const float* params_host) {
@@ -425,6 +485,15 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out) {
       t->t.stats.last_visible = cs.n_vis;
     }
     *out = t->t.stats;
+    unsigned long long churn[2];
+    TGS_CUDA(cudaStreamSynchronize(t->t.comp));
+    TGS_CUDA(cudaMemcpy(churn, t->t.churn_dev, sizeof(churn), cudaMemcpyDeviceToHost));
+    out->block_updates = churn[0];
+    out->cold_updates = churn[1];
+    out->host_cache_hits = t->t.tier.hits;
+    out->host_cache_misses = t->t.tier.misses;
+    out->log_bytes_read = t->t.tier.bytes_read;
+    out->log_bytes_written = t->t.tier.bytes_written;
     out->kernel_launches = g_launches;
     out->h2d_ms = t->t.copy_timer.ms[0];
     out->d2h_ms = t->t.copy_timer.ms[1];

@@ -1099,7 +1099,8 @@ __global__ void __launch_bounds__(PP_THREADS, 2) k_preprocess_bwd_batch(RenderLi
 // (4 per lane), a warp scan of the counts and one atomic per warp, so each
 // group's rows are written in ascending order (groups in any order).
 __global__ void k_touched_rows(const uint8_t* __restrict__ touched, uint64_t V, uint32_t* __restrict__ rows,
-                               uint32_t* __restrict__ count) {
+                               uint32_t* __restrict__ count, uint32_t* __restrict__ prows,
+                               uint32_t* __restrict__ pcount) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t g0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 128; g0 < V;
@@ -1123,12 +1124,36 @@ __global__ void k_touched_rows(const uint8_t* __restrict__ touched, uint64_t V, 
 #pragma unroll
     for (int e = 0; e < 4; ++e)
       if (f >> e & 1u) rows[base++] = (uint32_t)(p0 + e);
+    if (prows) {
+      // pairs (p0, p0 + 1) and (p0 + 2, p0 + 3) with a touched member:
+      // position | member mask << 30
+      const uint32_t ma = f & 3u, mb = (f >> 2) & 3u;
+      const uint32_t pc = (ma ? 1u : 0u) + (mb ? 1u : 0u);
+      uint32_t pinc = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, pinc, o);
+        if (lane >= o) pinc += y;
+      }
+      const uint32_t ptot = __shfl_sync(0xffffffffu, pinc, 31);
+      uint32_t pb = 0;
+      if (lane == 0 && ptot) pb = atomicAdd(pcount, ptot);
+      pb = __shfl_sync(0xffffffffu, pb, 0) + pinc - pc;
+      if (ma) prows[pb++] = (uint32_t)p0 | (ma << 30);
+      if (mb) prows[pb++] = (uint32_t)(p0 + 2) | (mb << 30);
+    }
   }
 }
 
-constexpr int ADAM_FG = 8;  // fields per thread
+constexpr int ADAM_FG = 4;  // fields per thread
 constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
 
+// One Gaussian's ADAM_FG fields f0.. of Adam: every load of the fields (the
+// gradient, both moments and the parameter) is issued before the first
+// update, so a thread keeps 4 ADAM_FG independent loads in flight; then the
+// updates and stores.  BF16 record: moments and SH-rest parameters are read
+// as BF16 and stored rounded (stochastically with one counter hash per
+// field: three 16-bit draws for m, v and the parameter).
 template <bool BF>
 __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __restrict__ grad,
                                          const float2* __restrict__ bias, const uint32_t* __restrict__ block_step,
@@ -1137,20 +1162,18 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
   const uint32_t B = rl.B;
   const float2 bc = bias[item];
   const float ic1 = bc.x, ic2 = bc.y;
-  float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
-  float* p = slot + lane;
+  float* __restrict__ slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+  float* __restrict__ p = slot + lane;
+  float gf[ADAM_FG], mf[ADAM_FG], vf[ADAM_FG], pf[ADAM_FG];
   if (!BF) {
-    // FP32 record: all loads of the row's fields first (independent, in
-    // flight together), then the updates and stores
-    float gf[ADAM_FG], mf[ADAM_FG], vf[ADAM_FG], pf[ADAM_FG];
-    float* m = p + rl.m_off;
-    float* v = p + rl.v_off;
+    float* __restrict__ m = p + rl.m_off;
+    float* __restrict__ v = p + rl.v_off;
 #pragma unroll
     for (int q = 0; q < ADAM_FG; ++q) {
       const int f = f0 + q;
       if (f < D) {
         const uint64_t o = (uint64_t)f * B;
-        gf[q] = grad[(uint64_t)f * V + i];
+        gf[q] = __ldg(grad + (uint64_t)f * V + i);
         mf[q] = m[o];
         vf[q] = v[o];
         pf[q] = p[o];
@@ -1169,11 +1192,20 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
       }
     }
   } else {
-    // BF16 record: field by field (a two-phase form costs occupancy here and
-    // measured slower)
-    __nv_bfloat16* q16 = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
-    __nv_bfloat16* m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
-    __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
+    __nv_bfloat16* __restrict__ q16 = reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane;
+    __nv_bfloat16* __restrict__ m = reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane;
+    __nv_bfloat16* __restrict__ v = reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane;
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        gf[q] = __ldg(grad + (uint64_t)f * V + i);
+        mf[q] = __bfloat162float(m[o]);
+        vf[q] = __bfloat162float(v[o]);
+        pf[q] = f < F_BF16 ? p[o] : __bfloat162float(q16[(uint64_t)(f - F_BF16) * B]);
+      }
+    }
     const bool sr = rl.sr != 0;
     const uint32_t blk = rl.item_block[item];
     const uint32_t step = block_step[blk];
@@ -1184,22 +1216,159 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
       const int f = f0 + q;
       if (f < D) {
         const uint64_t o = (uint64_t)f * B;
-        const float g = grad[(uint64_t)f * V + i];
-        const float mn = b1 * __bfloat162float(m[o]) + (1.f - b1) * g;
-        const float vn = b2 * __bfloat162float(v[o]) + (1.f - b2) * g * g;
+        const float mn = b1 * mf[q] + (1.f - b1) * gf[q];
+        const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
         const float upd = lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
-        // one counter hash per field: three 16-bit draws for m, v, parameter
         const uint64_t hsh = sr ? mix64(key0 + (uint64_t)f) : 0ull;
         m[o] = to_bf16(mn, sr, (uint32_t)hsh);
         v[o] = to_bf16(vn, sr, (uint32_t)(hsh >> 16));
+        if (f < F_BF16)
+          p[o] = pf[q] - upd;
+        else
+          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, (uint32_t)(hsh >> 32));
+      }
+    }
+  }
+}
+
+// Masked Adam on a pair of adjacent Gaussians (lanes l, l + 1 of one block,
+// l even; B even so a pair never straddles blocks): 8-byte FP32 / 4-byte
+// BF16 accesses for both, the item's slot, bias corrections and step counter
+// read once.  A member outside the mask keeps its values (stored back
+// unchanged).  Same arithmetic and rounding draws per Gaussian as adam_row.
+template <bool BF>
+__device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __restrict__ grad,
+                                          const float2* __restrict__ bias, const uint32_t* __restrict__ block_step,
+                                          uint64_t V, const LrSet& lrs, float b1, float b2, float eps, unsigned item,
+                                          unsigned lane, uint64_t i, uint32_t mask, int f0) {
+  const uint32_t B = rl.B;
+  const float2 bc = bias[item];
+  const float ic1 = bc.x, ic2 = bc.y;
+  float* __restrict__ slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+  const bool t0 = mask & 1u, t1 = mask & 2u;
+  float2 gf[ADAM_FG], mf[ADAM_FG], vf[ADAM_FG], pf[ADAM_FG];
+  if (!BF) {
+    float* __restrict__ p = slot + lane;
+    float* __restrict__ m = p + rl.m_off;
+    float* __restrict__ v = p + rl.v_off;
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        gf[q] = __ldg(reinterpret_cast<const float2*>(grad + (uint64_t)f * V + i));
+        mf[q] = *reinterpret_cast<const float2*>(m + o);
+        vf[q] = *reinterpret_cast<const float2*>(v + o);
+        pf[q] = *reinterpret_cast<const float2*>(p + o);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o = (uint64_t)f * B;
+        const float lr = lrs.g[lr_group(f)];
+        float2 mn, vn, pn;
+        mn.x = b1 * mf[q].x + (1.f - b1) * gf[q].x;
+        vn.x = b2 * vf[q].x + (1.f - b2) * gf[q].x * gf[q].x;
+        pn.x = pf[q].x - lr * (mn.x * ic1) / (sqrtf(vn.x * ic2) + eps);
+        mn.y = b1 * mf[q].y + (1.f - b1) * gf[q].y;
+        vn.y = b2 * vf[q].y + (1.f - b2) * gf[q].y * gf[q].y;
+        pn.y = pf[q].y - lr * (mn.y * ic1) / (sqrtf(vn.y * ic2) + eps);
+        if (!t0) { mn.x = mf[q].x; vn.x = vf[q].x; pn.x = pf[q].x; }
+        if (!t1) { mn.y = mf[q].y; vn.y = vf[q].y; pn.y = pf[q].y; }
+        *reinterpret_cast<float2*>(m + o) = mn;
+        *reinterpret_cast<float2*>(v + o) = vn;
+        *reinterpret_cast<float2*>(p + o) = pn;
+      }
+    }
+  } else {
+    float* __restrict__ p = slot + lane;
+    __nv_bfloat162* __restrict__ q16 =
+        reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(slot + (uint64_t)F_BF16 * B) + lane);
+    __nv_bfloat162* __restrict__ m =
+        reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(slot + rl.m_off) + lane);
+    __nv_bfloat162* __restrict__ v =
+        reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(slot + rl.v_off) + lane);
+    __nv_bfloat162 m16[ADAM_FG], v16[ADAM_FG], p16[ADAM_FG];
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o2 = (uint64_t)f * (B / 2);  // in pairs
+        gf[q] = __ldg(reinterpret_cast<const float2*>(grad + (uint64_t)f * V + i));
+        m16[q] = m[o2];
+        v16[q] = v[o2];
+        if (f < F_BF16)
+          pf[q] = *reinterpret_cast<const float2*>(p + (uint64_t)f * B);
+        else
+          p16[q] = q16[(uint64_t)(f - F_BF16) * (B / 2)];
+      }
+    }
+    const bool sr = rl.sr != 0;
+    const uint32_t blk = rl.item_block[item];
+    const uint32_t step = block_step[blk];
+    const uint64_t gid0 = (uint64_t)blk * B + lane;
+    const uint64_t salt = ((uint64_t)rl.seed << 40) ^ ((uint64_t)step << 20);
+    const uint64_t key0 = salt ^ (gid0 * 0x9E3779B97F4A7C15ull);
+    const uint64_t key1 = salt ^ ((gid0 + 1) * 0x9E3779B97F4A7C15ull);
+#pragma unroll
+    for (int q = 0; q < ADAM_FG; ++q) {
+      const int f = f0 + q;
+      if (f < D) {
+        const uint64_t o2 = (uint64_t)f * (B / 2);
+        const float lr = lrs.g[lr_group(f)];
+        const float2 mo = __bfloat1622float2(m16[q]), vo = __bfloat1622float2(v16[q]);
+        const float2 po = f < F_BF16 ? pf[q] : __bfloat1622float2(p16[q]);
+        const float mnx = b1 * mo.x + (1.f - b1) * gf[q].x, mny = b1 * mo.y + (1.f - b1) * gf[q].y;
+        const float vnx = b2 * vo.x + (1.f - b2) * gf[q].x * gf[q].x;
+        const float vny = b2 * vo.y + (1.f - b2) * gf[q].y * gf[q].y;
+        const float ux = lr * (mnx * ic1) / (sqrtf(vnx * ic2) + eps);
+        const float uy = lr * (mny * ic1) / (sqrtf(vny * ic2) + eps);
+        const uint64_t h0 = sr ? mix64(key0 + (uint64_t)f) : 0ull;
+        const uint64_t h1 = sr ? mix64(key1 + (uint64_t)f) : 0ull;
+        __nv_bfloat162 mw, vw;
+        mw.x = t0 ? to_bf16(mnx, sr, (uint32_t)h0) : m16[q].x;
+        mw.y = t1 ? to_bf16(mny, sr, (uint32_t)h1) : m16[q].y;
+        vw.x = t0 ? to_bf16(vnx, sr, (uint32_t)(h0 >> 16)) : v16[q].x;
+        vw.y = t1 ? to_bf16(vny, sr, (uint32_t)(h1 >> 16)) : v16[q].y;
+        m[o2] = mw;
+        v[o2] = vw;
         if (f < F_BF16) {
-          p[o] -= upd;
+          float2 pn = po;
+          if (t0) pn.x = po.x - ux;
+          if (t1) pn.y = po.y - uy;
+          *reinterpret_cast<float2*>(p + (uint64_t)f * B) = pn;
         } else {
-          const uint64_t o16 = (uint64_t)(f - F_BF16) * B;
-          q16[o16] = to_bf16(__bfloat162float(q16[o16]) - upd, sr, (uint32_t)(hsh >> 32));
+          __nv_bfloat162 pw;
+          pw.x = t0 ? to_bf16(po.x - ux, sr, (uint32_t)(h0 >> 32)) : p16[q].x;
+          pw.y = t1 ? to_bf16(po.y - uy, sr, (uint32_t)(h1 >> 32)) : p16[q].y;
+          q16[(uint64_t)(f - F_BF16) * (B / 2)] = pw;
         }
       }
     }
+  }
+}
+
+// Masked Adam over pairs of adjacent render-list positions with a touched
+// member (prows[0..*nprows): position | mask << 30), CTA (pair chunk, field
+// group).
+template <bool BF>
+__global__ void __launch_bounds__(PP_THREADS) k_adam_pairs(RenderList rl, const float* __restrict__ grad,
+                                                          const uint32_t* __restrict__ prows,
+                                                          const uint32_t* __restrict__ nprows,
+                                                          const float2* __restrict__ bias,
+                                                          const uint32_t* __restrict__ block_step, uint64_t V,
+                                                          LrSet lrs, float b1, float b2, float eps,
+                                                          const uint32_t* __restrict__ abort_flag) {
+  if (abort_flag && *abort_flag) return;  // a render of this step overflowed its pair capacity
+  const uint32_t B = rl.B, n = *nprows;
+  const int f0 = blockIdx.y * ADAM_FG;
+  for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
+    const uint32_t e = prows[t];
+    const uint32_t i = e & 0x3FFFFFFFu, mask = e >> 30;
+    const unsigned item = i / B, lane = i - item * B;
+    adam_pair<BF>(rl, grad, bias, block_step, V, lrs, b1, b2, eps, item, lane, i, mask, f0);
   }
 }
 
@@ -1227,15 +1396,24 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
 }
 
 __global__ void k_mark_touched(RenderList rl, const uint32_t* __restrict__ item_touched, uint32_t* block_step,
-                               uint8_t* dirty, uint32_t* abort_flag, float b1, float b2, float2* __restrict__ bias) {
+                               uint8_t* dirty, uint32_t* abort_flag, float b1, float b2, float2* __restrict__ bias,
+                               uint8_t* readmit, unsigned long long* churn) {
   unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
   if (abort_flag && abort_flag[0]) {
     if (j == 0) abort_flag[1] += 1;  // steps dropped since the overflow
     return;
   }
   if (j >= rl.n_items || !item_touched[j]) return;
-  const uint32_t st = block_step[rl.item_block[j]] + 1;
-  block_step[rl.item_block[j]] = st;
+  const uint32_t blk = rl.item_block[j];
+  const uint32_t st = block_step[blk] + 1;
+  block_step[blk] = st;
+  if (churn) {
+    atomicAdd(churn, 1ull);
+    if (readmit && readmit[blk]) {
+      atomicAdd(churn + 1, 1ull);
+      readmit[blk] = 0;
+    }
+  }
   if (dirty) dirty[rl.item_slot[j]] = 1;
   if (bias) {
     const float tau = (float)st;
@@ -1415,7 +1593,10 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.t_final, cs.cap_pix * sizeof(float)));
   TGS_CUDA(cudaMalloc(&cs.n_last, cs.cap_pix * sizeof(int)));
   TGS_CUDA(cudaMalloc(&cs.counters, 8 * sizeof(uint32_t)));
-  TGS_CUDA(cudaMallocHost(&cs.counters_host, 4 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMallocHost(&cs.counters_host, 8 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.bin_ctl, BIN_CTL_WORDS * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.status1, bin_status1_words(V) * sizeof(uint64_t)));
+  TGS_CUDA(cudaMemset(cs.status1, 0, bin_status1_words(V) * sizeof(uint64_t)));
   TGS_CUDA(cudaMalloc(&cs.torder, 2 * cs.cap_tiles * sizeof(uint32_t)));
   // backward split: up to 4 checkpoint slots per tile, at most 8192 (32 MB)
   TGS_CHECK(cs.cap_tiles < (1ull << 24), TGS_ERR_INVALID, "image has too many tiles");
@@ -1442,6 +1623,15 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
     cs.cap_pairs = cap;
     want = cap > cs.cap_v ? cap : cs.cap_v;
   }
+  const uint64_t sw = bin_status_words(cs.cap_v, cs.cap_pairs);
+  if (sw > cs.status_words) {
+    if (s) TGS_CUDA(cudaStreamSynchronize(s));
+    if (cs.status) TGS_CUDA(cudaFree(cs.status));
+    TGS_CUDA(cudaMalloc(&cs.status, sw * sizeof(uint64_t)));
+    // zero: no stale word carries a live epoch (epochs start at 1)
+    TGS_CUDA(cudaMemset(cs.status, 0, sw * sizeof(uint64_t)));
+    cs.status_words = sw;
+  }
   size_t sb = radix_scratch_bytes(want);
   size_t sc = scan_scratch_bytes(want);
   if (sc > sb) sb = sc;
@@ -1457,7 +1647,7 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
 void cam_state_free(CamState& cs) {
   void* ptrs[] = {cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.dkeys,
                   cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch,
-                  cs.torder, cs.ck, cs.tck, cs.units};
+                  cs.torder, cs.ck, cs.tck, cs.units, cs.bin_ctl, cs.status, cs.status1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (cs.counters_host) cudaFreeHost(cs.counters_host);
@@ -1495,22 +1685,7 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
     tm->end(StageTimer::PRE, s);
     tm->begin(StageTimer::SORT, s);
     // the sizes stay on the device: no host round trip inside a render
-    exclusive_scan_u32(cs.scan, cs.scan, nv_dev, V, cs.scratch, s);
-    k_compact_visible<<<div_up(V, 256), 256, 0, s>>>(V, cs.ntiles, cs.scan, cs.depth, cs.dkeys, cs.dvals);
-    TGS_LAUNCHED();
-    // the counts of an earlier render size the sorts' grids
-    radix_sort_pairs_dev(cs.dkeys, cs.dvals, cs.dkeys + cs.cap_v, cs.dvals + cs.cap_v, nv_dev, V, 32, cs.scratch, s,
-                         cs.hint_nv);
-    k_gather_counts<<<div_up(V, 256), 256, 0, s>>>(nv_dev, cs.dvals, cs.ntiles, cs.scan);
-    TGS_LAUNCHED();
-    exclusive_scan_u32_dev(cs.scan, cs.scan, np_dev, nv_dev, V, cs.scratch, s);
-    k_emit_pairs<<<4 * NSM, EP_THREADS, 0, s>>>(nv_dev, np_dev, cs.dvals, cs.rect, cs.scan, cam.TX, cs.pkeys,
-                                                cs.pvals, cs.cap_pairs, cs.counters + 2, cs.step_flag);
-    TGS_LAUNCHED();
-    radix_sort_pairs_dev(cs.pkeys, cs.pvals, cs.pkeys + cs.cap_pairs, cs.pvals + cs.cap_pairs, np_dev, cs.cap_pairs,
-                         bits_for(tiles), cs.scratch, s, cs.hint_np);
-    k_ranges<<<2 * NSM, 256, 0, s>>>(np_dev, cs.cap_pairs, cs.pkeys, cs.ranges);
-    TGS_LAUNCHED();
+    bin_and_sort(V, cam.TX, tiles, cs, s);
     k_tile_order<<<1, TO_THREADS, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.torder, cs.tck, cs.units,
                                           cs.counters + 5, cs.ck_cap);
     TGS_LAUNCHED();
@@ -1527,7 +1702,7 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   TGS_LAUNCHED();
   tm->end(StageTimer::FWD, s);
   // the counts reach the host asynchronously (read by cam_state_counts)
-  TGS_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TGS_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, 8 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   TGS_CUDA(cudaEventRecord(cs.ev_counts, s));
   cs.counts_pending = true;
 }
@@ -1541,6 +1716,8 @@ bool cam_state_counts(CamState& cs, bool wait) {
       if (e == cudaErrorNotReady) return false;
       TGS_CUDA(e);
     }
+    TGS_CHECK(cs.counters_host[6] == 0, TGS_ERR_TIMEOUT,
+              "a binning look-back wait ran out (its partition's predecessor never published)");
     cs.n_vis = cs.counters_host[0];
     cs.n_pairs = cs.counters_host[1];
     cs.overflow = cs.counters_host[2] != 0;
@@ -1678,19 +1855,37 @@ void render_backward_params(const RenderList& rl, const DevCam& cam, const CamSt
   TGS_LAUNCHED();
 }
 
-void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s) {
+void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s,
+                  uint32_t* prows, uint32_t* nprows) {
   TGS_CUDA(cudaMemsetAsync(nrows, 0, sizeof(uint32_t), s));
+  if (prows) TGS_CUDA(cudaMemsetAsync(nprows, 0, sizeof(uint32_t), s));
   const uint64_t V = rl.capacity();
   if (V == 0) return;
   const unsigned grid = std::min<uint64_t>(div_up(V, 128 * 8), 4 * NSM);
-  k_touched_rows<<<grid, 256, 0, s>>>(touched, V, rows, nrows);
+  k_touched_rows<<<grid, 256, 0, s>>>(touched, V, rows, nrows, prows, nprows);
   TGS_LAUNCHED();
 }
 
 void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
                       const float2* bias, const uint32_t* block_step, const LrSet& lr, float b1, float b2, float eps,
-                      cudaStream_t s, const uint32_t* abort_flag) {
+                      cudaStream_t s, const uint32_t* abort_flag, const uint32_t* prows, const uint32_t* nprows) {
   if (rl.capacity() == 0) return;
+  // the pair kernel reads FP32 fields as float2 and BF16 ones as bf16x2:
+  // every slot, field and moment array must start on an even float
+  const bool pairs_aligned = rl.B % 2 == 0 && rl.slot_stride % 2 == 0 && rl.m_off % 2 == 0 && rl.v_off % 2 == 0 &&
+                             (reinterpret_cast<uintptr_t>(rl.base) & 7u) == 0 &&
+                             (reinterpret_cast<uintptr_t>(grad) & 7u) == 0;
+  if (prows && pairs_aligned) {
+    const dim3 grid(std::min<uint64_t>(div_up(rl.capacity() / 2, PP_THREADS), 4 * NSM), ADAM_GROUPS);
+    if (rl.bf16)
+      k_adam_pairs<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, prows, nprows, bias, block_step, rl.capacity(), lr, b1,
+                                                    b2, eps, abort_flag);
+    else
+      k_adam_pairs<false><<<grid, PP_THREADS, 0, s>>>(rl, grad, prows, nprows, bias, block_step, rl.capacity(), lr,
+                                                     b1, b2, eps, abort_flag);
+    TGS_LAUNCHED();
+    return;
+  }
   const dim3 grid(std::min<uint64_t>(div_up(rl.capacity(), PP_THREADS), 4 * NSM), ADAM_GROUPS);
   if (rl.bf16)
     k_adam<true><<<grid, PP_THREADS, 0, s>>>(rl, grad, rows, nrows, bias, block_step, rl.capacity(), lr, b1, b2, eps,
@@ -1702,10 +1897,11 @@ void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* r
 }
 
 void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
-                         cudaStream_t s, uint32_t* abort_flag, float b1, float b2, float2* bias) {
+                         cudaStream_t s, uint32_t* abort_flag, float b1, float b2, float2* bias, uint8_t* readmit,
+                         unsigned long long* churn) {
   if (rl.n_items == 0) return;
   k_mark_touched<<<div_up(rl.n_items, 256), 256, 0, s>>>(rl, item_touched, block_step, dirty, abort_flag, b1, b2,
-                                                         bias);
+                                                         bias, readmit, churn);
   TGS_LAUNCHED();
 }
 

@@ -70,8 +70,15 @@ struct CamState {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   uint32_t* counters = nullptr;  // device [8]: n_vis, n_pairs (before the clamp), overflow, pairs needed, -,
-                                 // backward units
-  uint32_t* counters_host = nullptr;  // pinned mirror, copied at the end of each render
+                                 // backward units, binning look-back timeout
+  uint32_t* counters_host = nullptr;  // pinned mirror (8 words), copied at the end of each render
+  // binning (bin.cu): control words (digit counts and tickets, cleared per
+  // render), look-back status words tagged with a per-launch epoch
+  uint32_t* bin_ctl = nullptr;
+  uint64_t* status = nullptr;   // per-digit partition status of the radix passes
+  uint64_t* status1 = nullptr;  // partition status of compaction and pair emission
+  uint64_t status_words = 0;
+  uint32_t epoch = 0;
   cudaEvent_t ev_counts = nullptr;    // recorded after that copy
   uint32_t* step_flag = nullptr;      // optional device word raised with the overflow flag
   // results of the last render (valid after cam_state_counts)
@@ -82,6 +89,16 @@ struct CamState {
 };
 
 void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h);
+
+// Binning (bin.cu): digit-count and ticket words of one render, and the
+// look-back status words the binning kernels need for the given capacities.
+constexpr uint64_t BIN_CTL_WORDS = 8 * 256 + 16;
+uint64_t bin_status_words(uint64_t cap_v, uint64_t cap_pairs);
+uint64_t bin_status1_words(uint64_t cap_v);
+// Visible compaction, depth sort, pair emission, tile sort and tile ranges of
+// a render whose preprocess has run (V render-list positions, TX x (tiles /
+// TX) tiles); the counts stay on the device (cs.counters).
+void bin_and_sort(uint64_t V, int TX, uint64_t tiles, CamState& cs, cudaStream_t s);
 void cam_state_free(CamState& cs);
 void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
 // Reads the last render's counts into n_vis / n_pairs / overflow; wait =
@@ -132,8 +149,11 @@ void render_backward_params_batch(const RenderList& rl, const DevCam* cams, CamS
                                   const uint32_t* rows, const uint32_t* nrows, cudaStream_t s);
 
 // rows[0..*nrows) = the render-list positions with touched != 0 (groups of
-// 128 positions in ascending order, groups in any order).
-void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s);
+// 128 positions in ascending order, groups in any order).  prows (may be
+// null): the even positions i whose pair (i, i + 1) has a touched member, as
+// i | (touched[i] | touched[i + 1] << 1) << 30, their count in *nprows.
+void touched_rows(const RenderList& rl, const uint8_t* touched, uint32_t* rows, uint32_t* nrows, cudaStream_t s,
+                  uint32_t* prows = nullptr, uint32_t* nprows = nullptr);
 
 // Masked Adam over the listed (touched) rows of the render list: params and
 // moments in the pool are updated; `grad` is the local [59][rl.capacity()] array; step counters per
@@ -149,18 +169,23 @@ __host__ __device__ inline int lr_group(int f) {
 }
 
 // bias: per item (1 / (1 - b1^step), 1 / (1 - b2^step)) from mark_touched_blocks.
+// prows / nprows (may be null; used when B is even): the pair list of
+// touched_rows -- each thread then updates two adjacent Gaussians.
 void adam_render_list(const RenderList& rl, const float* grad, const uint32_t* rows, const uint32_t* nrows,
                       const float2* bias, const uint32_t* block_step, const LrSet& lr, float b1, float b2, float eps,
-                      cudaStream_t s, const uint32_t* abort_flag = nullptr);
+                      cudaStream_t s, const uint32_t* abort_flag = nullptr, const uint32_t* prows = nullptr,
+                      const uint32_t* nprows = nullptr);
 
 // Per-item bookkeeping before Adam: for items with item_touched != 0,
 // block_step[block] += 1 and dirty[slot] = 1.  While abort_flag[0] is set
 // (device, may be null) nothing is marked and abort_flag[1] counts the step.
 // bias (per item, may be null) receives the Adam bias corrections of the
 // incremented step.
+// readmit (per block, may be null): set for a re-admitted block; its next
+// update counts as cold-restarted (Tab. 9) and clears it.  churn (may be null): [0] += updated blocks, [1] += cold-restarted ones.
 void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uint32_t* block_step, uint8_t* dirty,
                          cudaStream_t s, uint32_t* abort_flag = nullptr, float b1 = 0.9f, float b2 = 0.999f,
-                         float2* bias = nullptr);
+                         float2* bias = nullptr, uint8_t* readmit = nullptr, unsigned long long* churn = nullptr);
 
 // touched[j * B + l] |= (Gaussian l of item j had a non-empty tile rect in cs).
 void mark_visible_bytes(const RenderList& rl, const CamState& cs, uint8_t* touched, cudaStream_t s);

@@ -2,11 +2,15 @@
 // HBM working-set cache of block slots, the copy streams and the step.
 //
 // Streams: `ctl` runs Level-1 culling and Algorithm 1, `h2d` streams S+ into
-// slots, `d2h` writes dirty S- blocks back, `comp` renders and trains.  With
-// the exact next-batch prefetch, batch t+1's delta is selected at the start
-// of step t and its incoming blocks are copied into spare slots while batch t
-// computes (Sec. 3.4 "Hierarchical asynchronous execution"); blocks that can
-// only go into slots freed by S- are copied after that write-back.
+// free slots, `h2d_late` into the slots S- frees (after their write-back),
+// `d2h` writes dirty S- blocks back, `tgtq` uploads host targets, `comp`
+// renders and trains.  With the exact next-batch prefetch, batch t+1's delta
+// is selected at the start of step t and its incoming blocks are copied into
+// spare slots while batch t computes (Sec. 3.4 "Hierarchical asynchronous
+// execution"); blocks that can only go into slots freed by S- are copied
+// after that write-back.  Every copy waits only for what it needs (the slot's
+// last reader and write-back, the block's own pending write-back), so no
+// copy queues behind one that waits for compute.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -105,9 +109,11 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   TGS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   TGS_CUDA(cudaStreamCreateWithPriority(&comp, cudaStreamNonBlocking, prio_low));
   TGS_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
+  TGS_CUDA(cudaStreamCreateWithFlags(&h2d_late, cudaStreamNonBlocking));
+  TGS_CUDA(cudaStreamCreateWithFlags(&tgtq, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
   TGS_CUDA(cudaStreamCreateWithPriority(&ctl, cudaStreamNonBlocking, prio_high));
-  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_ctl, &ev_user, &ev_wb, &ev_snap, &ev_tgt_ready, &ev_tgt_used[0],
+  for (cudaEvent_t* e : {&ev_comp, &ev_h2d, &ev_h2d_late, &ev_ctl, &ev_user, &ev_wb, &ev_snap, &ev_tgt_ready, &ev_tgt_used[0],
                          &ev_tgt_used[1]})
     TGS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   TGS_CUDA(cudaEventCreate(&ev_stall_a));
@@ -146,11 +152,21 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   }
 
   // ---- host tier: K block records [params | m | v], field-major inside
-  TGS_CUDA(cudaHostAlloc((void**)&host, K * rec_floats * sizeof(float), cudaHostAllocPortable));
-  if (ck)
-    ck_read(ck, host, K * rec_floats * sizeof(float));
-  else
+  tier.init(K, rec_floats, c.host_cache_blocks, c.backing_path);
+  if (ck) {
+    if (!tier.tiered) {
+      ck_read(ck, tier.pinned, K * rec_floats * sizeof(float));
+    } else {
+      std::vector<float> rec(rec_floats);
+      for (uint64_t k = 0; k < K; ++k) {
+        ck_read(ck, rec.data(), rec_floats * sizeof(float));
+        tier.put_initial((uint32_t)k, rec.data());
+      }
+      tier.finish_initial();
+    }
+  } else {
     fill_host(params);
+  }
 
   // ---- device cache and state
   dalloc(pool, n_slots * rec_floats);
@@ -158,6 +174,8 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   dalloc(spheres_snap, K);
   dalloc(ages, K);
   dalloc(block_step, K);
+  dalloc(readmit_dev, K);
+  dalloc(churn_dev, 2);
   dalloc(dirty_dev, n_slots);
   TGS_CUDA(cudaMemsetAsync(ages, 0, K * sizeof(uint32_t), comp));
   {
@@ -186,9 +204,14 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   dalloc(rb.counters, 16);
   TGS_CUDA(cudaMalloc(&rb.scratch, residency_scratch_bytes(K)));
   dalloc(lists_dev, 3 * K + 16);
-  TGS_CUDA(cudaMallocHost(&lists_host, (3 * K + 16) * sizeof(uint32_t)));
-  TGS_CUDA(cudaMallocHost(&kvis_host_pinned, (uint64_t)vis_rows * words * sizeof(uint32_t)));
-  TGS_CUDA(cudaMallocHost(&r_host_pinned, words * sizeof(uint32_t)));
+  // the selection's results arrive in mapped pinned memory (device stores)
+  TGS_CUDA(cudaHostAlloc((void**)&lists_host, (3 * K + 16) * sizeof(uint32_t), cudaHostAllocMapped));
+  TGS_CUDA(cudaHostAlloc((void**)&kvis_host_pinned, (uint64_t)vis_rows * words * sizeof(uint32_t), cudaHostAllocMapped));
+  TGS_CUDA(cudaHostAlloc((void**)&r_host_pinned, words * sizeof(uint32_t), cudaHostAllocMapped));
+  std::memset(lists_host, 0, (3 * K + 16) * sizeof(uint32_t));
+  TGS_CUDA(cudaHostGetDevicePointer((void**)&lists_map, lists_host, 0));
+  TGS_CUDA(cudaHostGetDevicePointer((void**)&kvis_map, kvis_host_pinned, 0));
+  TGS_CUDA(cudaHostGetDevicePointer((void**)&r_map, r_host_pinned, 0));
   dalloc(rl_dev, 3ull * max_items);
   TGS_CUDA(cudaMallocHost(&rl_host, RL_RING * 3ull * max_items * sizeof(uint32_t)));
   for (auto& e : rl_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -215,6 +238,7 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   dalloc(item_bias, max_items);
   V_cap_rows = V_cap;
   dalloc(rows_dev, V_cap + 1);  // touched rows, then their count
+  dalloc(prows_dev, V_cap / 2 + 2);  // touched pairs, then their count
   dalloc(grad_local, (uint64_t)D * V_cap);
   dalloc(loss_dev, 4);
   TGS_CUDA(cudaMallocHost(&loss_host, 4 * sizeof(float)));
@@ -240,6 +264,8 @@ void Table::create(const tgs_config& c, uint64_t n, const float* params, std::FI
   dirty_host.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
   wb_pending.assign(K, 0);
+  admitted_at.assign(K, 0);
+  resident_count = 0;
   slot_free_ev.assign(n_slots, nullptr);
   slot_has_ev.assign(n_slots, 0);
   for (auto& e : slot_free_ev) TGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -255,8 +281,10 @@ void Table::fill_host(const float* params) {
   const bool bf = cfg.host_bf16 != 0;
   for (unsigned w = 0; w < nt; ++w)
     th.emplace_back([&, w]() {
+      // tiered: the record is built here and written to the log
+      std::vector<float> buf(tier.tiered ? rec_floats : 0);
       for (uint64_t k = w; k < K; k += nt) {
-        float* rec = host + k * rec_floats;
+        float* rec = tier.tiered ? buf.data() : tier.pinned + k * rec_floats;
         __nv_bfloat16* rec16 = reinterpret_cast<__nv_bfloat16*>(rec + (uint64_t)F_BF16 * B);
         std::memset(rec + p_floats, 0, 2 * m_floats * sizeof(float));
         for (uint32_t l = 0; l < B; ++l) {
@@ -270,9 +298,11 @@ void Table::fill_host(const float* params) {
               rec[(uint64_t)f * B + l] = x;
           }
         }
+        if (tier.tiered) tier.put_initial((uint32_t)k, rec);
       }
     });
   for (auto& t : th) t.join();
+  tier.finish_initial();
 }
 
 // Bounding spheres of every block: means and log-scales of the host records
@@ -281,8 +311,17 @@ void Table::init_spheres() {
   uint64_t chunk = std::min<uint64_t>(n_slots, max_items);
   for (uint64_t k0 = 0; k0 < K; k0 += chunk) {
     uint64_t m = std::min(chunk, K - k0);
-    TGS_CUDA(cudaMemcpy2DAsync(pool, rec_floats * sizeof(float), host + k0 * rec_floats, rec_floats * sizeof(float),
-                               6ull * B * sizeof(float), m, cudaMemcpyHostToDevice, comp));
+    if (!tier.tiered) {
+      TGS_CUDA(cudaMemcpy2DAsync(pool, rec_floats * sizeof(float), tier.pinned + k0 * rec_floats,
+                                 rec_floats * sizeof(float), 6ull * B * sizeof(float), m, cudaMemcpyHostToDevice, comp));
+    } else {
+      for (uint64_t j = 0; j < m; ++j) {
+        const uint32_t blk = (uint32_t)(k0 + j);
+        TGS_CUDA(cudaMemcpyAsync(pool + j * rec_floats, tier.acquire_read(blk), 6ull * B * sizeof(float),
+                                 cudaMemcpyHostToDevice, comp));
+        tier.record_use(blk, comp);
+      }
+    }
     for (uint64_t j = 0; j < m; ++j) {
       uint64_t blk = k0 + j;
       rl_host[j] = (uint32_t)j;
@@ -302,7 +341,8 @@ void Table::init_spheres() {
 // moments and step counters and empties the cache.
 void Table::set_params(const float* params) {
   TGS_CHECK(params, TGS_ERR_INVALID, "tgs_set_params: null params");
-  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  for (cudaStream_t st : {comp, h2d, h2d_late, tgtq, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  tier.reset_log();
   fill_host(params);
   std::vector<uint32_t> a(K, 126u);
   TGS_CUDA(cudaMemcpy(ages, a.data(), K * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -318,6 +358,9 @@ void Table::set_params(const float* params) {
   slot_has_ev.assign(n_slots, 0);
   ever_loaded.assign(K, 0);
   wb_pending.assign(K, 0);
+  admitted_at.assign(K, 0);
+  resident_count = 0;
+  TGS_CUDA(cudaMemset(readmit_dev, 0, K));
   prep = Prepared();
   init_spheres();
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
@@ -327,15 +370,18 @@ void Table::set_params(const float* params) {
 void Table::destroy() {
   if (comp) cudaStreamSynchronize(comp);
   if (h2d) cudaStreamSynchronize(h2d);
+  if (h2d_late) cudaStreamSynchronize(h2d_late);
+  if (tgtq) cudaStreamSynchronize(tgtq);
   if (d2h) cudaStreamSynchronize(d2h);
   if (ctl) cudaStreamSynchronize(ctl);
   for (auto& cs : cams) cam_state_free(cs);
-  void* dev[] = {pool, spheres, spheres_snap, ages, block_step, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
+  void* dev[] = {pool, spheres, spheres_snap, ages, block_step, readmit_dev, churn_dev, dirty_dev, r_bits, r_next_bits, acc_bits, acc_next_bits, kvis,
                  kvis_union, planes_dev, rb.flag, rb.pos, rb.key, rb.blk, rb.sel, rb.tmp, rb.tmp2, rb.counters,
-                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, ssim_buf, touched, item_touched, item_bias, rows_dev, grad_local,
+                 rb.scratch, lists_dev, rl_dev, images, dl_dimg, targets_buf, ssim_buf, touched, item_touched, item_bias, rows_dev, prows_dev, grad_local,
                  loss_dev, abort_dev};
   for (void* p : dev) dfree(p);
-  void* hst[] = {host, planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host,
+  tier.release();
+  void* hst[] = {planes_host, lists_host, rl_host, loss_host, kvis_host_pinned, r_host_pinned, abort_host,
                  loss_ring};
   for (void* p : hst)
     if (p) cudaFreeHost(p);
@@ -343,10 +389,10 @@ void Table::destroy() {
     if (e) cudaEventDestroy(e);
   for (auto& e : rl_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap, ev_tgt_ready,
+  for (cudaEvent_t e : {ev_comp, ev_h2d, ev_h2d_late, ev_ctl, ev_user, ev_stall_a, ev_stall_b, ev_wb, ev_snap, ev_tgt_ready,
                         ev_tgt_used[0], ev_tgt_used[1]})
     if (e) cudaEventDestroy(e);
-  for (cudaStream_t s : {comp, h2d, d2h, ctl})
+  for (cudaStream_t s : {comp, h2d, h2d_late, tgtq, d2h, ctl})
     if (s) cudaStreamDestroy(s);
 }
 
@@ -430,16 +476,13 @@ void Table::select_enqueue(uint32_t J, Prepared& out, bool accessed) {
   if (quota * J > C) quota = C / J;
   residency(acc_bits, r_bits, kvis, kvis_union, (int)J, K, ages, C, cfg.lambda, quota, r_next_bits,
             lists_dev, lists_dev + K, lists_dev + 2 * K, acc_next_bits, rb, ctl, accessed);
-  // counts and the three lists in full (one read-back, one host wait)
-  TGS_CUDA(cudaMemcpyAsync(lists_host, rb.counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
-  TGS_CUDA(cudaMemcpyAsync(lists_host + 16, lists_dev, 3 * K * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
-  TGS_CUDA(cudaMemcpyAsync(kvis_host_pinned, kvis, (uint64_t)J * words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                           ctl));
-  TGS_CUDA(cudaEventRecord(ev_ctl, ctl));
   // the selected set becomes the current one for the next selection
   std::swap(r_bits, r_next_bits);
   if (accessed) std::swap(acc_bits, acc_next_bits);
-  TGS_CUDA(cudaMemcpyAsync(r_host_pinned, r_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctl));
+  // counts, the used list prefixes, the visible rows and the selected set
+  // reach the host by device stores into mapped memory (one host wait)
+  publish_sets(rb.counters, lists_dev, K, kvis, (uint64_t)J * words, r_bits, words, lists_map, kvis_map, r_map, ctl);
+  TGS_CUDA(cudaEventRecord(ev_ctl, ctl));
   out.enqueued = true;
 }
 
@@ -562,7 +605,7 @@ void Table::prepare_finish(Prepared& out) {
 static void copy_block_in(Table& t, uint32_t b, uint32_t s, cudaStream_t st) {
   const uint64_t pf = t.p_floats;
   float* dst = t.pool + (uint64_t)s * t.rec_floats;
-  const float* src = t.host + (uint64_t)b * t.rec_floats;
+  const float* src = t.tier.acquire_read(b);
   if (t.slot_has_ev[s]) TGS_CUDA(cudaStreamWaitEvent(st, t.slot_free_ev[s], 0));
   // a block evicted earlier may still be on its way back to the host tier:
   // wait for the latest write-back batch (it includes this block's)
@@ -572,18 +615,25 @@ static void copy_block_in(Table& t, uint32_t b, uint32_t s, cudaStream_t st) {
   }
   if (t.cfg.moments_policy == 1) {
     TGS_CUDA(cudaMemcpyAsync(dst, src, pf * sizeof(float), cudaMemcpyHostToDevice, st));
+    t.tier.record_use(b, st);
     TGS_CUDA(cudaMemsetAsync(dst + pf, 0, 2 * t.m_floats * sizeof(float), st));
     TGS_CUDA(cudaMemsetAsync(t.block_step + b, 0, sizeof(uint32_t), st));
     t.stats.bytes_h2d += pf * sizeof(float);
     t.stats.cold_restarts++;
   } else {
     TGS_CUDA(cudaMemcpyAsync(dst, src, t.rec_floats * sizeof(float), cudaMemcpyHostToDevice, st));
+    t.tier.record_use(b, st);
     t.stats.bytes_h2d += t.rec_floats * sizeof(float);
   }
+  // Tab. 9: the block's next update is its first after a re-admission
+  // (under moments_policy 1 it starts from zeroed moments)
+  if (t.ever_loaded[b]) TGS_CUDA(cudaMemsetAsync(t.readmit_dev + b, 1, 1, st));
   t.dirty_host[s] = 0;
   t.stats.blocks_in++;
   if (t.ever_loaded[b]) t.stats.readmissions++;
   t.ever_loaded[b] = 1;
+  t.admitted_at[b] = t.stats.steps;
+  t.resident_count++;
 }
 
 void Table::issue_early(Prepared& p) {
@@ -610,8 +660,9 @@ void Table::issue_evictions_and_late(Prepared& p) {
     uint32_t b = p.plan.evict_block[i], s = p.plan.evict_slot[i];
     if (dirty_host[s]) {
       uint64_t nf = cfg.moments_policy == 1 ? pf : rec_floats;
-      TGS_CUDA(cudaMemcpyAsync(host + (uint64_t)b * rec_floats, pool + (uint64_t)s * rec_floats, nf * sizeof(float),
-                               cudaMemcpyDeviceToHost, d2h));
+      TGS_CUDA(cudaMemcpyAsync(tier.acquire_write(b, nf == rec_floats), pool + (uint64_t)s * rec_floats,
+                               nf * sizeof(float), cudaMemcpyDeviceToHost, d2h));
+      tier.record_use(b, d2h);
       stats.bytes_d2h += nf * sizeof(float);
       stats.writebacks++;
       wb_pending[b] = 1;
@@ -620,19 +671,26 @@ void Table::issue_evictions_and_late(Prepared& p) {
     TGS_CUDA(cudaEventRecord(slot_free_ev[s], d2h));
     slot_has_ev[s] = 1;
     stats.blocks_out++;
+    stats.streaks++;
+    stats.streak_steps += stats.steps - admitted_at[b];
+    resident_count--;
   }
   if (any_wb) {
     copy_timer.end(1, d2h);
     TGS_CUDA(cudaEventRecord(ev_wb, d2h));
   }
-  TGS_CUDA(cudaStreamWaitEvent(h2d, ev_comp, 0));
+  // loads into the slots S- frees wait (slot_free_ev) for the compute that
+  // last read those slots and for their write-back; on their own stream,
+  // so that the next selection's loads into free slots (and the host
+  // targets) do not queue behind them
+  if (!cfg.overlap) TGS_CUDA(cudaStreamWaitEvent(h2d_late, ev_comp, 0));
   if (!p.plan.late_block.empty()) {
-    copy_timer.begin(0, h2d);
+    copy_timer.begin(0, h2d_late);
     for (size_t i = 0; i < p.plan.late_block.size(); ++i)
-      copy_block_in(*this, p.plan.late_block[i], p.plan.late_slot[i], h2d);
-    copy_timer.end(0, h2d);
+      copy_block_in(*this, p.plan.late_block[i], p.plan.late_slot[i], h2d_late);
+    copy_timer.end(0, h2d_late);
   }
-  TGS_CUDA(cudaEventRecord(ev_h2d, h2d));
+  TGS_CUDA(cudaEventRecord(ev_h2d_late, h2d_late));
 }
 
 void Table::collect_stall() {
@@ -655,6 +713,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
   // wait for this batch's incoming blocks; the wait is the exposed copy time
   TGS_CUDA(cudaEventRecord(ev_stall_a, comp));
   TGS_CUDA(cudaStreamWaitEvent(comp, ev_h2d, 0));
+  TGS_CUDA(cudaStreamWaitEvent(comp, ev_h2d_late, 0));
   TGS_CUDA(cudaEventRecord(ev_stall_b, comp));
   stall_pending = true;
   const float* tgt = targets_dev;
@@ -671,9 +730,9 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
       tgt_buf = tgt_parity;
       tgt_parity ^= 1;
       float* dst = targets_buf + (uint64_t)tgt_buf * cfg.max_batch * pix * 3;
-      if (tgt_used[tgt_buf]) TGS_CUDA(cudaStreamWaitEvent(h2d, ev_tgt_used[tgt_buf], 0));
-      TGS_CUDA(cudaMemcpyAsync(dst, targets_host, (uint64_t)J * pix * 3 * sizeof(float), cudaMemcpyHostToDevice, h2d));
-      TGS_CUDA(cudaEventRecord(ev_tgt_ready, h2d));
+      if (tgt_used[tgt_buf]) TGS_CUDA(cudaStreamWaitEvent(tgtq, ev_tgt_used[tgt_buf], 0));
+      TGS_CUDA(cudaMemcpyAsync(dst, targets_host, (uint64_t)J * pix * 3 * sizeof(float), cudaMemcpyHostToDevice, tgtq));
+      TGS_CUDA(cudaEventRecord(ev_tgt_ready, tgtq));
       tgt = dst;
     }
   }
@@ -716,7 +775,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     }
     TGS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), comp));
     // the rows the chain rule stores and the optimiser updates
-    touched_rows(rl, touched, rows_dev, rows_dev + V_cap_rows, comp);
+    touched_rows(rl, touched, rows_dev, rows_dev + V_cap_rows, comp, prows_dev, prows_dev + V_cap / 2 + 1);
     timer.begin(StageTimer::LOSS, comp);
     if (cfg.loss == 2)
       photometric_loss_ssim(images, tgt, (int)J, W, H, dl_dimg, loss_dev, ssim_buf, comp);
@@ -752,9 +811,10 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     }
     timer.end(StageTimer::PBWD, comp);
     timer.begin(StageTimer::ADAM, comp);
-    mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias);
+    mark_touched_blocks(rl, item_touched, block_step, dirty_dev, comp, abort_dev, cfg.beta1, cfg.beta2, item_bias,
+                        readmit_dev, churn_dev);
     adam_render_list(rl, grad_local, rows_dev, rows_dev + V_cap_rows, item_bias, block_step, step_lrs(),
-                     cfg.beta1, cfg.beta2, cfg.eps, comp, abort_dev);
+                     cfg.beta1, cfg.beta2, cfg.eps, comp, abort_dev, prows_dev, prows_dev + V_cap / 2 + 1);
     timer.end(StageTimer::ADAM, comp);
     // the next batch's cull (control stream) reads the bounds first
     TGS_CUDA(cudaStreamWaitEvent(comp, ev_ctl, 0));
@@ -762,6 +822,7 @@ void Table::compute(const Prepared& p, const float* targets_dev, const float* ta
     block_bounds(rl, item_touched, spheres, comp, abort_dev);
     timer.end(StageTimer::BOUNDS, comp);
     for (uint32_t j = 0; j < n_items; ++j) dirty_host[p.render_slots[j]] = 1;
+    stats.resident_block_steps += resident_count;
     stats.steps++;
   }
   TGS_CUDA(cudaEventRecord(ev_comp, comp));
@@ -881,7 +942,7 @@ bool Table::check_overflow(bool wait) {
     if (cs.pairs_needed > need) need = cs.pairs_needed;
   }
   if (!any) return false;
-  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  for (cudaStream_t st : {comp, h2d, h2d_late, tgtq, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
   TGS_CUDA(cudaMemcpy(abort_host, abort_dev, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   stats.dropped_steps += abort_host[1];
   stats.pair_overflows += 1;
@@ -922,7 +983,7 @@ static void ck_write(std::FILE* f, const void* src, uint64_t bytes) {
 
 void Table::save(const char* path) {
   flush();
-  for (cudaStream_t st : {comp, h2d, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
+  for (cudaStream_t st : {comp, h2d, h2d_late, tgtq, d2h, ctl}) TGS_CUDA(cudaStreamSynchronize(st));
   std::FILE* f = std::fopen(path, "wb");
   TGS_CHECK(f, TGS_ERR_INVALID, std::string("cannot open checkpoint for writing: ") + path);
   try {
@@ -930,7 +991,10 @@ void Table::save(const char* path) {
     ck_write(f, kCkMagic, sizeof(kCkMagic));
     ck_write(f, hdr, sizeof(hdr));
     ck_write(f, perm.data(), N * sizeof(uint32_t));
-    ck_write(f, host, K * rec_floats * sizeof(float));
+    if (!tier.tiered)
+      ck_write(f, tier.pinned, K * rec_floats * sizeof(float));
+    else
+      for (uint64_t k = 0; k < K; ++k) ck_write(f, tier.acquire_read((uint32_t)k), rec_floats * sizeof(float));
     std::vector<uint32_t> u(K);
     TGS_CUDA(cudaMemcpy(u.data(), block_step, K * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     ck_write(f, u.data(), K * sizeof(uint32_t));
@@ -971,16 +1035,15 @@ void Table::resume(const tgs_config& c, const char* path) {
 
 // Consistency barrier: every dirty resident block goes back to the host tier.
 void Table::flush() {
-  TGS_CUDA(cudaStreamSynchronize(comp));
-  TGS_CUDA(cudaStreamSynchronize(h2d));
-  TGS_CUDA(cudaStreamSynchronize(d2h));
+  for (cudaStream_t st : {comp, h2d, h2d_late, tgtq, d2h}) TGS_CUDA(cudaStreamSynchronize(st));
   const uint64_t pf = p_floats;
   for (uint64_t s = 0; s < n_slots; ++s) {
     int64_t b = block_of_slot[s];
     if (b < 0 || !dirty_host[s]) continue;
     uint64_t nf = cfg.moments_policy == 1 ? pf : rec_floats;
-    TGS_CUDA(cudaMemcpyAsync(host + (uint64_t)b * rec_floats, pool + s * rec_floats, nf * sizeof(float),
-                             cudaMemcpyDeviceToHost, d2h));
+    TGS_CUDA(cudaMemcpyAsync(tier.acquire_write((uint32_t)b, nf == rec_floats), pool + s * rec_floats,
+                             nf * sizeof(float), cudaMemcpyDeviceToHost, d2h));
+    tier.record_use((uint32_t)b, d2h);
     dirty_host[s] = 0;
   }
   TGS_CUDA(cudaStreamSynchronize(d2h));

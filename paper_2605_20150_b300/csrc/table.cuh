@@ -6,6 +6,7 @@
 
 #include <deque>
 
+#include "host_tier.cuh"
 #include "predictor.cuh"
 #include "raster.cuh"
 #include "visibility.cuh"
@@ -42,8 +43,8 @@ struct Table {
   uint64_t V_cap = 0;        // render-list Gaussians capacity
   uint32_t max_items = 0;
 
-  // host tier
-  float* host = nullptr;     // pinned, K records
+  // host tier: K records pinned, or a pinned pool over a log file
+  HostTier tier;
   std::vector<uint32_t> perm;
 
   // device state
@@ -62,6 +63,7 @@ struct Table {
   uint32_t* lists_host = nullptr;  // pinned
   uint32_t* kvis_host_pinned = nullptr;  // pinned, max_batch x words
   uint32_t* r_host_pinned = nullptr;     // pinned, words
+  uint32_t *lists_map = nullptr, *kvis_map = nullptr, *r_map = nullptr;  // device views of the three (mapped)
   uint32_t* rl_dev = nullptr;      // item_slot | item_count | item_block
   static constexpr uint32_t RL_RING = 4;
   uint32_t* rl_host = nullptr;     // pinned, RL_RING staging slots of 3 x max_items
@@ -88,6 +90,7 @@ struct Table {
   float2* item_bias = nullptr;     // per render-list item: Adam bias corrections of this step
   uint32_t* rows_dev = nullptr;    // touched render-list rows of this step, count at rows_dev[V_cap_rows]
   uint64_t V_cap_rows = 0;
+  uint32_t* prows_dev = nullptr;   // pairs of adjacent positions with a touched member, count at prows_dev[V_cap / 2 + 1]
   uint32_t* abort_dev = nullptr;   // [2]: a render of a step overflowed its pairs; steps dropped since
   uint32_t* abort_host = nullptr;  // pinned
 
@@ -99,6 +102,10 @@ struct Table {
   std::vector<uint8_t> slot_has_ev;
   std::vector<uint8_t> ever_loaded;      // K: for the re-admission counter
   std::vector<uint8_t> wb_pending;       // K: write-back to the host tier issued, not yet waited on
+  std::vector<uint64_t> admitted_at;     // K: stats.steps when the block was last admitted (Tab. 9 streaks)
+  uint64_t resident_count = 0;           // blocks holding a slot
+  uint8_t* readmit_dev = nullptr;        // K: moments zeroed by a re-admission, not yet updated
+  unsigned long long* churn_dev = nullptr;  // [2]: block updates, cold-restarted block updates
   std::deque<uint32_t> free_fifo;        // free slots, longest free first
   cudaEvent_t ev_wb = nullptr;           // recorded after each write-back batch on d2h
   cudaEvent_t ev_snap = nullptr;         // recorded after the bounds snapshot on comp
@@ -110,8 +117,11 @@ struct Table {
   std::vector<uint32_t> last_r_host;     // words
   Prepared prep;
 
-  cudaStream_t comp = nullptr, h2d = nullptr, d2h = nullptr, ctl = nullptr;
-  cudaEvent_t ev_comp = nullptr, ev_h2d = nullptr, ev_ctl = nullptr, ev_user = nullptr;
+  // h2d: loads into free slots; h2d_late: loads into slots S- frees (they
+  // wait for that write-back), kept off h2d so that later loads into free
+  // slots never queue behind them; tgtq: host targets of a step
+  cudaStream_t comp = nullptr, h2d = nullptr, h2d_late = nullptr, tgtq = nullptr, d2h = nullptr, ctl = nullptr;
+  cudaEvent_t ev_comp = nullptr, ev_h2d = nullptr, ev_h2d_late = nullptr, ev_ctl = nullptr, ev_user = nullptr;
   cudaEvent_t ev_stall_a = nullptr, ev_stall_b = nullptr;
   bool stall_pending = false;
 

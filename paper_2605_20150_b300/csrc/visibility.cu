@@ -570,4 +570,34 @@ void residency(const uint32_t* k_acc, const uint32_t* r_cur, const uint32_t* k_n
   TGS_LAUNCHED();
 }
 
+namespace {
+
+// The selection's results written into mapped host memory by device stores:
+// the counts and the used prefixes of the three lists, the visibility rows and
+// the resident bitmap.  A copy-engine read-back would queue behind the bulk
+// block copies of the same direction (tens of MB of write-back) and keep the
+// host waiting for them.
+__global__ void k_publish_sets(const uint32_t* __restrict__ counters, const uint32_t* __restrict__ lists, uint64_t K,
+                               const uint32_t* __restrict__ kvis, uint64_t kvis_words,
+                               const uint32_t* __restrict__ rbits, uint64_t words, uint32_t* out_lists,
+                               uint32_t* out_kvis, uint32_t* out_r) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t n[3] = {counters[0], counters[1], counters[2]};
+  if (tid < 4) out_lists[tid] = counters[tid];
+  for (int q = 0; q < 3; ++q)
+    for (uint64_t i = tid; i < n[q] && i < K; i += stride) out_lists[16 + q * K + i] = lists[q * K + i];
+  for (uint64_t i = tid; i < kvis_words; i += stride) out_kvis[i] = kvis[i];
+  for (uint64_t i = tid; i < words; i += stride) out_r[i] = rbits[i];
+}
+
+}  // namespace
+
+void publish_sets(const uint32_t* counters, const uint32_t* lists, uint64_t K, const uint32_t* kvis,
+                  uint64_t kvis_words, const uint32_t* rbits, uint64_t words, uint32_t* out_lists, uint32_t* out_kvis,
+                  uint32_t* out_r, cudaStream_t s) {
+  k_publish_sets<<<8, 256, 0, s>>>(counters, lists, K, kvis, kvis_words, rbits, words, out_lists, out_kvis, out_r);
+  TGS_LAUNCHED();
+}
+
 }  // namespace tgs

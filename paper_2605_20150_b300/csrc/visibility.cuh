@@ -58,4 +58,12 @@ void residency(const uint32_t* k_acc, const uint32_t* r_cur, const uint32_t* k_n
 
 size_t residency_scratch_bytes(uint64_t K);
 
+// Writes the selection's results (counters[0..3], the used prefixes of the
+// three lists of K entries, kvis_words visibility words, the resident bitmap)
+// into host memory mapped for the device (out_*: device views of mapped
+// pinned buffers; out_lists holds 16 + 3K words: counts, then the lists).
+void publish_sets(const uint32_t* counters, const uint32_t* lists, uint64_t K, const uint32_t* kvis,
+                  uint64_t kvis_words, const uint32_t* rbits, uint64_t words, uint32_t* out_lists, uint32_t* out_kvis,
+                  uint32_t* out_r, cudaStream_t s);
+
 }  // namespace tgs

@@ -25,12 +25,15 @@ def bf16_ulp(x):
     return 2.0 ** (e - 7)
 
 
-def test_bf16_step_matches_oracle(orc, tgs):
-    c, perm, Pm, tp = c1_inputs(orc)
+# 1250: the BF16 record's slots start on odd floats (Adam per Gaussian);
+# 1000: even slot, moment and field offsets (Adam on pairs of Gaussians)
+@pytest.mark.parametrize("B", [1250, 1000])
+def test_bf16_step_matches_oracle(orc, tgs, B):
+    c, perm, Pm, tp = c1_inputs(orc, block_size=B)
     cams = [scenes.camera_array(x) for x in c["cams"]]
-    _, Pt = orc.create(tp, 1250)
+    _, Pt = orc.create(tp, B)
     target = orc.render(Pt.astype(np.float64), cams[0])["img"].astype(np.float32)
-    table = tgs.TideTable(c["params"], block_size=1250, max_batch=1, max_width=256, max_height=256, loss=1,
+    table = tgs.TideTable(c["params"], block_size=B, max_batch=1, max_width=256, max_height=256, loss=1,
                           host_bf16=1, stochastic_round=1)
     table.step([c["cams"][0]], target[None])
     # oracle on the BF16-rounded table
@@ -38,10 +41,10 @@ def test_bf16_step_matches_oracle(orc, tgs):
     Pb[:, 14:] = bf16_round(Pm[:, 14:])
     P0 = Pb.copy()
     M1, M2 = np.zeros_like(Pb), np.zeros_like(Pb)
-    steps = np.zeros(16, np.int64)
-    sph = orc.block_spheres(Pm.astype(np.float64), 1250)
+    steps = np.zeros((Pm.shape[0] + B - 1) // B, np.int64)
+    sph = orc.block_spheres(Pm.astype(np.float64), B)
     _, vis = orc.visible_blocks(sph, [cams[0]])
-    o = orc.train_step(Pb, M1, M2, steps, 1250, np.nonzero(vis)[0], [cams[0]], target[None], lr=1e-3,
+    o = orc.train_step(Pb, M1, M2, steps, B, np.nonzero(vis)[0], [cams[0]], target[None], lr=1e-3,
                        loss_kind=1)
     rec = table.camera_record(0, 256, 256)
     err, frac = image_within(rec["image"], o["records"][0])

@@ -194,3 +194,90 @@ def test_ablation_without_morton_order_renders_the_same_image(tgs):
         t.close()
     d = np.abs(imgs[0] - imgs[1])
     assert d.max() < 1e-3 and (d > 1e-6).mean() < 0.01
+
+
+def test_streamed_sequence_matches_oracle(orc, tgs):
+    """Out-of-core parity over a camera sequence (Sec. 3.4-3.5): a cache of
+    kmax + 2 of the 80 blocks, so every step evicts, writes dirty blocks back
+    and re-admits blocks evicted earlier; lr 1e-3, moments stream with their
+    block.  The oracle trains step by step on the GPU's render sets (the
+    blocks of R_t & K_t); after every step the block spheres match the
+    oracle's parameters (bound refresh), and after the final consistency
+    barrier the whole state does: parameters within one Adam step of sign
+    noise at no more than 0.05% of the entries (the update direction of a
+    near-zero gradient may flip between FP32 and FP64) and 1e-5 elsewhere,
+    first moments to 1e-3, step counters exactly.  A write-back that dropped
+    an update, or a re-admission that read a stale record, moves a whole
+    block by a step and fails the count."""
+    cfg = scenes.small_cube_config()
+    P0 = cfg["params"]
+    B = 250
+    cams = _cams()
+    perm, Pm = orc.create(P0, B)
+    K = (P0.shape[0] + B - 1) // B
+    sph = orc.block_spheres(Pm.astype(np.float64), B)
+    kmax = max(int(orc.visible_blocks(sph, [scenes.camera_array(c)])[1].sum()) for c in cams)
+    seq = [cams[i % 4] for i in range(10)]
+    tgt = np.zeros((1, 160, 192, 3), np.float32) + 0.2
+    vir = tgs.TideTable(P0, block_size=B, max_batch=1, max_width=192, max_height=160, loss=1, prefetch_mode=0,
+                        moments_policy=0, lr=1e-3, cache_blocks=kmax + 2, spare_slots=4)
+    P = Pm.astype(np.float64).copy()
+    M1, M2 = np.zeros_like(P), np.zeros_like(P)
+    steps = np.zeros(K, np.int64)
+    for c in seq:
+        lv = vir.step([c], tgt)
+        sets = vir.sets(1)
+        blocks = np.nonzero(sets["k_visible"] & sets["r_resident"])[0]
+        o = orc.train_step(P, M1, M2, steps, B, blocks, [scenes.camera_array(c)], tgt, lr=1e-3, loss_kind=1)
+        assert abs(lv - o["loss"]) <= 1e-4 * o["loss"]
+        np.testing.assert_allclose(vir.spheres(), orc.block_spheres(P, B), rtol=0, atol=5e-3)
+    st = vir.stats()
+    assert st["blocks_out"] > 0 and st["writebacks"] > 0 and st["readmissions"] > 0
+    pg, mg, vg, sg = vir.state()
+    assert np.array_equal(sg, steps.astype(np.uint32))
+    d = np.abs(pg.astype(np.float64) - P)
+    flips = d > 1e-5
+    assert flips.mean() < 5e-4, flips.sum()
+    assert d.max() <= 5e-3, d.max()  # a few Adam steps of lr 1e-3
+    np.testing.assert_allclose(mg, M1, rtol=1e-3, atol=2e-7)
+    vir.close()
+
+
+def test_host_tier_over_a_log_file_equals_pinned_host(tgs, tmp_path):
+    """The host second tier (Sec. 3.4, a CPU cache over storage): 12 pinned
+    record slots over an append-only log file for 80 blocks, under a GPU
+    cache of kmax + 2 blocks, so blocks are read back from the log and dirty
+    write-backs are appended to it.  The camera sequence trains the same as
+    with every record pinned in host memory (the runs differ only in the order
+    of float atomics, as in the virtualised-equals-resident test), and the
+    counters show pool misses, log reads and appended records."""
+    cfg = scenes.small_cube_config()
+    P = cfg["params"]
+    B = 250
+    cams = _cams()
+    seq = [cams[i % 4] for i in range(10)]
+    tgt = np.zeros((1, 160, 192, 3), np.float32) + 0.2
+    common = dict(block_size=B, max_batch=1, max_width=192, max_height=160, loss=1, prefetch_mode=1,
+                  moments_policy=0, lr=1e-3, cache_blocks=52, spare_slots=4)
+    pin = tgs.TideTable(P, **common)
+    log = tgs.TideTable(P, host_cache_blocks=12, backing_path=str(tmp_path / "tier.log"), **common)
+    assert (tmp_path / "tier.log").stat().st_size >= 80 * 250 * 708
+    for i, c in enumerate(seq):
+        nxt = [seq[i + 1]] if i + 1 < len(seq) else None
+        lp = pin.step([c], tgt, next_cams=nxt)
+        ll = log.step([c], tgt, next_cams=nxt)
+        assert abs(lp - ll) <= 1e-5 * max(lp, 1e-6)
+    pp, mp, vp, sp = pin.state()
+    pl, ml, vl, sl = log.state()
+    assert np.array_equal(sp, sl)
+    d = np.abs(pp.astype(np.float64) - pl.astype(np.float64))
+    assert (d <= 1e-6).mean() > 0.9999 and d.max() < 5e-3
+    np.testing.assert_allclose(ml, mp, rtol=1e-3, atol=1e-9)
+    st = log.stats()
+    assert st["host_cache_misses"] > 0 and st["log_bytes_read"] > 0
+    assert st["log_bytes_written"] > 80 * 250 * 708  # the initial records plus appended dirty blocks
+    assert st["writebacks"] > 0 and st["readmissions"] > 0
+    assert pin.stats()["host_cache_misses"] == 0
+    pin.close()
+    log.close()
+    assert not (tmp_path / "tier.log").exists()  # the log goes with its table
