@@ -9,8 +9,9 @@
 //  emission in depth order + stable tile sort (the tile/depth order of the
 //  pairs equals a stable sort of (tile << 32 | depth bits) keys emitted in id
 //  order, with far fewer radix passes over the pairs).
-//  k_raster_fwd      one CTA per 16x16 tile (64 threads x 4 pixels), 128 splats staged in
-//                    shared memory, front-to-back blending with the 0.99 clamp,
+//  k_raster_fwd      one CTA per 16x16 tile (8 warps of 8 x 4 pixels, one
+//                    pixel per thread), 32 splats per warp staged in shared
+//                    memory, front-to-back blending with the 0.99 clamp,
 //                    the 1/255 skip and the T < 1e-4 stop.
 //  k_raster_bwd      reverse traversal from each pixel's last contributor,
 //                    recomputing T_i = T_{i+1} / (1 - alpha_i); per-Gaussian
@@ -47,6 +48,22 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+// Rounding draws of Adam's BF16 stores: one SplitMix64 finaliser per
+// Gaussian and step gives a 32-bit key; per field, the MurmurHash3 32-bit
+// finaliser (Appleby) of key + f * golden gives 32 bits (m draw low 16, v
+// draw high 16) and, for a BF16 parameter, a second finaliser 16 more.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t sr_key(uint32_t seed, uint64_t gid, uint32_t step) {
+  return (uint32_t)mix64(((uint64_t)seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20));
 }
 
 // FP32 -> BF16: round to nearest even, or stochastically with the 16 random
@@ -510,23 +527,40 @@ __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, cons
 // pixels are saturated (forward) and starts at the largest n_last of its
 // pixels (backward), without waiting for the other warps.  A backward CTA
 // takes one unit: a whole tile, or one list segment of a split tile.
-constexpr int R_PPT = 2;
+constexpr int R_PPT = 2;                     // backward: pixels per thread
 constexpr int R_THREADS = TILE_PIX / R_PPT;  // 128
 constexpr int R_WARPS = R_THREADS / 32;
+// Forward: one pixel per thread, 8 warps of 8 x 4 pixels.  The forward's
+// time is set by its longest warps (the tiles whose lists saturate last);
+// half the pixels per thread halves a warp's work per splat, and the smaller
+// square passes fewer splats.  The backward keeps two pixels per thread: its
+// per-splat warp reduction is then shared by 64 pixels.
+constexpr int F_PPT = 1;
+constexpr int F_THREADS = TILE_PIX / F_PPT;  // 256
 
 struct WarpPix {
   int px, py0;     // this thread's column and first row
+  int lx, ly0;     // the same inside the tile (checkpoint index (ly0 + k) * TILE + lx)
   float wx0, wy0;  // the warp square's first column and row
+  float wh;        // its height - 1 (its width is 8)
 };
+// Warp w of a tile owns the 8-column square at columns (w & 1) * 8 and rows
+// (w >> 1) * 4 PPT .. + 4 PPT - 1; lane l its column l & 7 and rows
+// (l >> 3) * PPT .. + PPT - 1.
+template <int PPT>
 __device__ __forceinline__ WarpPix warp_pixels(int tile, int TX) {
+  constexpr int RH = 4 * PPT;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   WarpPix q;
-  const int x0 = (tile % TX) * TILE + (w & 1) * 8;
-  const int y0 = (tile / TX) * TILE + (w >> 1) * 8;
-  q.px = x0 + (l & 7);
-  q.py0 = y0 + (l >> 3) * R_PPT;
-  q.wx0 = (float)x0;
-  q.wy0 = (float)y0;
+  const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
+  const int sx = (w & 1) * 8, sy = (w >> 1) * RH;
+  q.lx = sx + (l & 7);
+  q.ly0 = sy + (l >> 3) * PPT;
+  q.px = tx0 + q.lx;
+  q.py0 = ty0 + q.ly0;
+  q.wx0 = (float)(tx0 + sx);
+  q.wy0 = (float)(ty0 + sy);
+  q.wh = (float)(RH - 1);
   return q;
 }
 
@@ -549,7 +583,7 @@ __device__ __forceinline__ float edge_min_y(float b, float lo, float hi, float A
 __device__ __forceinline__ bool splat_hits(const WarpPix& q, float x, float y, float A, float B, float C, float o) {
   const float L = logf(255.f * o);
   if (!(L > 0.f)) return false;
-  const float ax0 = q.wx0 - x, ax1 = ax0 + 7.f, by0 = q.wy0 - y, by1 = by0 + 7.f;
+  const float ax0 = q.wx0 - x, ax1 = ax0 + 7.f, by0 = q.wy0 - y, by1 = by0 + q.wh;
   if (ax0 <= 0.f && ax1 >= 0.f && by0 <= 0.f && by1 >= 0.f) return true;
   float m = edge_min_x(ax0, by0, by1, A, B, C);
   m = fminf(m, edge_min_x(ax1, by0, by1, A, B, C));
@@ -580,7 +614,8 @@ __device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, 
   return splat_hits(q, g.x, g.y, co.x, co.y, co.z, co.w);
 }
 
-__global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restrict__ ranges,
+template <int PPT>
+__global__ void __launch_bounds__(TILE_PIX / PPT) k_raster_fwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ pvals,
                                                          const float2* __restrict__ xy,
                                                          const float4* __restrict__ conic_o,
@@ -590,9 +625,9 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
                                                          const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ tck,
                                                          float4* __restrict__ ck) {
-  __shared__ Splat s_sp[R_WARPS][32];
+  __shared__ Splat s_sp[TILE_PIX / PPT / 32][32];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
-  const WarpPix q = warp_pixels(tile, TX);
+  const WarpPix q = warp_pixels<PPT>(tile, TX);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
@@ -602,12 +637,12 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
   const uint32_t ck0 = tck ? tck[tile] : ~0u;
   const int ns = (int)seg_count((uint32_t)n);
   const float fpx = (float)q.px;
-  float T[R_PPT], C0[R_PPT], C1[R_PPT], C2[R_PPT];
-  int last[R_PPT];
-  bool live[R_PPT];
+  float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+  int last[PPT];
+  bool live[PPT];
   bool act = false;
 #pragma unroll
-  for (int k = 0; k < R_PPT; ++k) {
+  for (int k = 0; k < PPT; ++k) {
     T[k] = 1.f;
     C0[k] = C1[k] = C2[k] = 0.f;
     last[k] = 0;
@@ -615,11 +650,13 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
     act |= live[k];
   }
   bool going = __any_sync(0xffffffffu, act);
+  int wrote = 0;  // boundary slots written (slot i - 1: the state before position i R_SEG)
   for (int b = 0; b < n && going; b += 32) {
     if (ck0 != ~0u && b > 0 && b % R_SEG == 0 && b / R_SEG < ns) {
-      float4* c = ck + (uint64_t)(ck0 + b / R_SEG - 1) * TILE_PIX + threadIdx.x;
+      float4* c = ck + (uint64_t)(ck0 + b / R_SEG - 1) * TILE_PIX + q.lx;
 #pragma unroll
-      for (int k = 0; k < R_PPT; ++k) c[k * R_THREADS] = make_float4(T[k], C0[k], C1[k], C2[k]);
+      for (int k = 0; k < PPT; ++k) c[(q.ly0 + k) * TILE] = make_float4(T[k], C0[k], C1[k], C2[k]);
+      wrote = b / R_SEG;
     }
     const bool hit = b + lane < n && stage_splat(pvals, xy, conic_o, rgb, r.x + b + lane, q, &sp[lane]);
     __syncwarp();
@@ -636,7 +673,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
       const float dx = __fsub_rn(fpx, a.x);
       const float adxx = __fmul_rn(a.z, __fmul_rn(dx, dx));
 #pragma unroll
-      for (int k = 0; k < R_PPT; ++k) {
+      for (int k = 0; k < PPT; ++k) {
         const float dy = __fsub_rn((float)(q.py0 + k), a.y);
         const float qf = __fadd_rn(adxx, __fmul_rn(bb.x, __fmul_rn(dy, dy)));
         const float power = __fsub_rn(__fmul_rn(-0.5f, qf), __fmul_rn(a.w, __fmul_rn(dx, dy)));
@@ -663,12 +700,17 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_fwd(const uint2* __restric
     __syncwarp();  // the batch slots are rewritten next
   }
   if (ck0 != ~0u) {
-    float4* c = ck + (uint64_t)(ck0 + ns - 1) * TILE_PIX + threadIdx.x;
+    // a warp that saturated early holds its final state at every boundary it
+    // did not reach: the backward's squares need not be this warp's, and a
+    // backward warp reads the boundary states of all its pixels
+    for (int i = wrote; i < ns; ++i) {
+      float4* c = ck + (uint64_t)(ck0 + i) * TILE_PIX + q.lx;
 #pragma unroll
-    for (int k = 0; k < R_PPT; ++k) c[k * R_THREADS] = make_float4(T[k], C0[k], C1[k], C2[k]);
+      for (int k = 0; k < PPT; ++k) c[(q.ly0 + k) * TILE] = make_float4(T[k], C0[k], C1[k], C2[k]);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < R_PPT; ++k) {
+  for (int k = 0; k < PPT; ++k) {
     const int py = q.py0 + k;
     if (q.px < W && py < H) {
       uint64_t pix = (uint64_t)py * W + q.px;
@@ -708,7 +750,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
     tile = (int)(u & 0xFFFFFFu);
     seg = (int)(u >> 24);
   }
-  const WarpPix q = warp_pixels(tile, TX);
+  const WarpPix q = warp_pixels<R_PPT>(tile, TX);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Splat* sp = s_sp[wid];
   const uint2 r = ranges[tile];
@@ -751,11 +793,11 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
   if (wlast > b1) {
     // the segment lies below the warp's last contribution: start from the
     // forward's state at b1, T = T(b1) and S_c = (C_c final - C_c(b1)) / T(b1)
-    const float4* cf = ck + (uint64_t)(ck0 + ns - 1) * TILE_PIX + threadIdx.x;
-    const float4* c1 = ck + (uint64_t)(ck0 + seg) * TILE_PIX + threadIdx.x;
+    const float4* cf = ck + (uint64_t)(ck0 + ns - 1) * TILE_PIX + q.lx;
+    const float4* c1 = ck + (uint64_t)(ck0 + seg) * TILE_PIX + q.lx;
 #pragma unroll
     for (int k = 0; k < R_PPT; ++k) {
-      const float4 f = cf[k * R_THREADS], a = c1[k * R_THREADS];
+      const float4 f = cf[(q.ly0 + k) * TILE], a = c1[(q.ly0 + k) * TILE];
       T[k] = a.x;
       Qs[k] = (gr[k] * (f.y - a.y) + gg[k] * (f.z - a.z) + gb[k] * (f.w - a.w)) / a.x;
     }
@@ -1188,7 +1230,7 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
         m[o] = mn;
         v[o] = vn;
-        p[o] = pf[q] - lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
+        p[o] = pf[q] - lrs.g[lr_group(f)] * __fdividef(mn * ic1, sqrtf(vn * ic2) + eps);
       }
     }
   } else {
@@ -1208,9 +1250,7 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
     }
     const bool sr = rl.sr != 0;
     const uint32_t blk = rl.item_block[item];
-    const uint32_t step = block_step[blk];
-    const uint64_t gid = (uint64_t)blk * B + lane;
-    const uint64_t key0 = ((uint64_t)rl.seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20);
+    const uint32_t key = sr ? sr_key(rl.seed, (uint64_t)blk * B + lane, block_step[blk]) : 0u;
 #pragma unroll
     for (int q = 0; q < ADAM_FG; ++q) {
       const int f = f0 + q;
@@ -1218,14 +1258,14 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         const uint64_t o = (uint64_t)f * B;
         const float mn = b1 * mf[q] + (1.f - b1) * gf[q];
         const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
-        const float upd = lrs.g[lr_group(f)] * (mn * ic1) / (sqrtf(vn * ic2) + eps);
-        const uint64_t hsh = sr ? mix64(key0 + (uint64_t)f) : 0ull;
-        m[o] = to_bf16(mn, sr, (uint32_t)hsh);
-        v[o] = to_bf16(vn, sr, (uint32_t)(hsh >> 16));
+        const float upd = lrs.g[lr_group(f)] * __fdividef(mn * ic1, sqrtf(vn * ic2) + eps);
+        const uint32_t h = sr ? fmix32(key + (uint32_t)f * 0x9E3779B9u) : 0u;
+        m[o] = to_bf16(mn, sr, h);
+        v[o] = to_bf16(vn, sr, h >> 16);
         if (f < F_BF16)
           p[o] = pf[q] - upd;
         else
-          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, (uint32_t)(hsh >> 32));
+          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, sr ? fmix32(h ^ 0x27D4EB2Fu) : 0u);
       }
     }
   }
@@ -1271,10 +1311,10 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
         float2 mn, vn, pn;
         mn.x = b1 * mf[q].x + (1.f - b1) * gf[q].x;
         vn.x = b2 * vf[q].x + (1.f - b2) * gf[q].x * gf[q].x;
-        pn.x = pf[q].x - lr * (mn.x * ic1) / (sqrtf(vn.x * ic2) + eps);
+        pn.x = pf[q].x - lr * __fdividef(mn.x * ic1, sqrtf(vn.x * ic2) + eps);
         mn.y = b1 * mf[q].y + (1.f - b1) * gf[q].y;
         vn.y = b2 * vf[q].y + (1.f - b2) * gf[q].y * gf[q].y;
-        pn.y = pf[q].y - lr * (mn.y * ic1) / (sqrtf(vn.y * ic2) + eps);
+        pn.y = pf[q].y - lr * __fdividef(mn.y * ic1, sqrtf(vn.y * ic2) + eps);
         if (!t0) { mn.x = mf[q].x; vn.x = vf[q].x; pn.x = pf[q].x; }
         if (!t1) { mn.y = mf[q].y; vn.y = vf[q].y; pn.y = pf[q].y; }
         *reinterpret_cast<float2*>(m + o) = mn;
@@ -1309,9 +1349,8 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
     const uint32_t blk = rl.item_block[item];
     const uint32_t step = block_step[blk];
     const uint64_t gid0 = (uint64_t)blk * B + lane;
-    const uint64_t salt = ((uint64_t)rl.seed << 40) ^ ((uint64_t)step << 20);
-    const uint64_t key0 = salt ^ (gid0 * 0x9E3779B97F4A7C15ull);
-    const uint64_t key1 = salt ^ ((gid0 + 1) * 0x9E3779B97F4A7C15ull);
+    const uint32_t key0 = sr ? sr_key(rl.seed, gid0, step) : 0u;
+    const uint32_t key1 = sr ? sr_key(rl.seed, gid0 + 1, step) : 0u;
 #pragma unroll
     for (int q = 0; q < ADAM_FG; ++q) {
       const int f = f0 + q;
@@ -1323,15 +1362,15 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
         const float mnx = b1 * mo.x + (1.f - b1) * gf[q].x, mny = b1 * mo.y + (1.f - b1) * gf[q].y;
         const float vnx = b2 * vo.x + (1.f - b2) * gf[q].x * gf[q].x;
         const float vny = b2 * vo.y + (1.f - b2) * gf[q].y * gf[q].y;
-        const float ux = lr * (mnx * ic1) / (sqrtf(vnx * ic2) + eps);
-        const float uy = lr * (mny * ic1) / (sqrtf(vny * ic2) + eps);
-        const uint64_t h0 = sr ? mix64(key0 + (uint64_t)f) : 0ull;
-        const uint64_t h1 = sr ? mix64(key1 + (uint64_t)f) : 0ull;
+        const float ux = lr * __fdividef(mnx * ic1, sqrtf(vnx * ic2) + eps);
+        const float uy = lr * __fdividef(mny * ic1, sqrtf(vny * ic2) + eps);
+        const uint32_t h0 = sr ? fmix32(key0 + (uint32_t)f * 0x9E3779B9u) : 0u;
+        const uint32_t h1 = sr ? fmix32(key1 + (uint32_t)f * 0x9E3779B9u) : 0u;
         __nv_bfloat162 mw, vw;
-        mw.x = t0 ? to_bf16(mnx, sr, (uint32_t)h0) : m16[q].x;
-        mw.y = t1 ? to_bf16(mny, sr, (uint32_t)h1) : m16[q].y;
-        vw.x = t0 ? to_bf16(vnx, sr, (uint32_t)(h0 >> 16)) : v16[q].x;
-        vw.y = t1 ? to_bf16(vny, sr, (uint32_t)(h1 >> 16)) : v16[q].y;
+        mw.x = t0 ? to_bf16(mnx, sr, h0) : m16[q].x;
+        mw.y = t1 ? to_bf16(mny, sr, h1) : m16[q].y;
+        vw.x = t0 ? to_bf16(vnx, sr, h0 >> 16) : v16[q].x;
+        vw.y = t1 ? to_bf16(vny, sr, h1 >> 16) : v16[q].y;
         m[o2] = mw;
         v[o2] = vw;
         if (f < F_BF16) {
@@ -1341,8 +1380,8 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
           *reinterpret_cast<float2*>(p + (uint64_t)f * B) = pn;
         } else {
           __nv_bfloat162 pw;
-          pw.x = t0 ? to_bf16(po.x - ux, sr, (uint32_t)(h0 >> 32)) : p16[q].x;
-          pw.y = t1 ? to_bf16(po.y - uy, sr, (uint32_t)(h1 >> 32)) : p16[q].y;
+          pw.x = t0 ? to_bf16(po.x - ux, sr, sr ? fmix32(h0 ^ 0x27D4EB2Fu) : 0u) : p16[q].x;
+          pw.y = t1 ? to_bf16(po.y - uy, sr, sr ? fmix32(h1 ^ 0x27D4EB2Fu) : 0u) : p16[q].y;
           q16[(uint64_t)(f - F_BF16) * (B / 2)] = pw;
         }
       }
@@ -1354,7 +1393,7 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
 // member (prows[0..*nprows): position | mask << 30), CTA (pair chunk, field
 // group).
 template <bool BF>
-__global__ void __launch_bounds__(PP_THREADS) k_adam_pairs(RenderList rl, const float* __restrict__ grad,
+__global__ void __launch_bounds__(PP_THREADS, 3) k_adam_pairs(RenderList rl, const float* __restrict__ grad,
                                                           const uint32_t* __restrict__ prows,
                                                           const uint32_t* __restrict__ nprows,
                                                           const float2* __restrict__ bias,
@@ -1695,7 +1734,7 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
     cs.order_valid = false;
   }
   tm->begin(StageTimer::FWD, s);
-  k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+  k_raster_fwd<F_PPT><<<(unsigned)tiles, F_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last,
                                                    cs.order_valid ? cs.torder : nullptr,
                                                    cs.order_valid ? cs.tck : nullptr, cs.ck);
@@ -1780,7 +1819,7 @@ void render_forward_fixed(const RenderList& rl, const DevCam& cam, const float b
       TGS_LAUNCHED();
     }
   }
-  k_raster_fwd<<<(unsigned)tiles, R_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
+  k_raster_fwd<F_PPT><<<(unsigned)tiles, F_THREADS, 0, s>>>(cs.ranges, cs.pvals, cs.xy, cs.conic_o, cs.rgb, cam.W, cam.H,
                                                    cam.TX, bg3, image, cs.t_final, cs.n_last, nullptr, nullptr,
                                                    nullptr);
   cs.order_valid = false;
