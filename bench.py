@@ -42,7 +42,7 @@ METRIC = "train iters/s, learned+BF16 vs plain FP32 path at <=0.1 dB PSNR gap; l
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=800)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="street100m", choices=["aerial2m", "street100m", "city"])
@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--cams", type=int, default=None)
     ap.add_argument("--cache-gb", type=float, default=24.0, help="HBM working-set cache cap (street workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="street workload: only the headline form's W + K steps (NVTX range timed:headline), "
+                         "for profiler runs; prints a reduced line")
     ap.add_argument("--ablation", action="store_true",
                     help="street: also time the Tab. 5 ablations (no differential streaming, no overlap, no Morton) and the Shuffle camera order")
     return ap.parse_args()
@@ -513,7 +516,7 @@ def run_street(args, rank, world, local):
                 moments_policy=0, loss=2)
     table = tgs.TideTable(host, prefetch_mode=0, **base)
     targets, vis = drive_targets(torch, table, cams, dev)
-    targets_f, vis_f = drive_targets(torch, table, fast, dev)
+    targets_f, vis_f = drive_targets(torch, table, fast, dev) if not args.profile else (None, None)
     spheres = torch.tensor(table.spheres(), device=dev)
     torch.cuda.synchronize()
     chunk = 1 << 24
@@ -523,12 +526,16 @@ def run_street(args, rank, world, local):
         host[a:a + chunk] = rows.cpu().numpy()
     t_setup = time.perf_counter() - t0
     tb = tgs.TideTable(host, prefetch_mode=2, host_bf16=1, stochastic_round=1, **base)
-    forms, pred, t_train = drive_forms(torch, tgs, table, tb, host, cams, targets, vis, spheres, world, local, dev,
-                                       head_rec=True)
-    # at 80 m per frame two frames ahead is twice the delta: the link-bound
-    # drive prefetches the next frame only, at a stricter threshold
-    forms_fast, _, t_train_f = drive_forms(torch, tgs, table, tb, host, fast, targets_f, vis_f, spheres, world,
-                                           local, dev, threshold=0.5, horizon_mask=0b01)
+    if args.profile:
+        pred, t_train = train_predictor(tgs, torch, vis, spheres, cams, dev)
+        tb.set_params(host)
+    else:
+        forms, pred, t_train = drive_forms(torch, tgs, table, tb, host, cams, targets, vis, spheres, world, local,
+                                           dev, head_rec=True)
+        # at 80 m per frame two frames ahead is twice the delta: the link-bound
+        # drive prefetches the next frame only, at a stricter threshold
+        forms_fast, _, t_train_f = drive_forms(torch, tgs, table, tb, host, fast, targets_f, vis_f, spheres, world,
+                                               local, dev, threshold=0.5, horizon_mask=0b01)
     del targets_f
     table.close()
     del table
@@ -554,10 +561,12 @@ def run_street(args, rank, world, local):
     torch.cuda.synchronize()
     rank_barrier(world)
     clk.mark()
+    torch.cuda.nvtx.range_push("timed:headline")
     e0.record(s)
     for k in range(args.warmup, args.warmup + args.steps):
         one(k)
     e1.record(s)
+    torch.cuda.nvtx.range_pop()
     tb.sync()
     torch.cuda.synchronize()
     clk.mark(end=True)
@@ -565,6 +574,16 @@ def run_street(args, rank, world, local):
     clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     launches = tb.stats()["kernel_launches"] - st0["kernel_launches"]
+    if args.profile:
+        tb.stage_timing(True)
+        tb.stage_ms(reset=True)
+        for k in range(STAGE_STEPS):
+            one(k)
+        tb.sync()
+        stages = tb.stage_ms(reset=True)
+        tb.close()
+        return {"profile": True, "ms": ms, "launches": launches, "clocks": clocks, "n": n,
+                "stages": {kk: round(v[0] / STAGE_STEPS, 4) for kk, v in stages.items()}}
     drive_b = drive_b_eval(args, tgs, tb, pred, host, base, dev)
     ablation = ablation_eval(args, tgs, host, base, cams, targets, train_ids) if args.ablation else None
     peak = link_peak(torch)
@@ -1098,6 +1117,13 @@ def main():
     else:
         res = run_street(args, rank, world, local) if street else run_ours(args, rank, world, local)
     ms_step = res["ms"] / args.steps
+    if res.get("profile"):
+        if rank == 0:
+            print(json.dumps({"profile": "street headline form only (not a benchmark line)", "ms_per_step":
+                              round(ms_step, 4), "steps": args.steps, "warmup": args.warmup,
+                              "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
+                              "stages_ms_per_step": res["stages"]}))
+        return
     value = job_iters_per_s(world, ms_step)
     e2e_ms = max_over_ranks(res["e2e_ms"], world)
     if street:

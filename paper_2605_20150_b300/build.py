@@ -5,7 +5,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = ["sort.cu", "bin.cu", "visibility.cu", "raster.cu", "table.cu", "predictor.cu", "api.cu", "noalloc.cu", "ssim.cu", "host_tier.cu"]
+SRC = ["sort.cu", "tiles.cu", "visibility.cu", "raster.cu", "table.cu", "predictor.cu", "api.cu", "noalloc.cu", "ssim.cu", "host_tier.cu"]
 LIB = os.path.join(HERE, "libtidegs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-v",

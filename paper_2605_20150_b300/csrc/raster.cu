@@ -15,8 +15,9 @@
 //                    the 1/255 skip and the T < 1e-4 stop.
 //  k_raster_bwd      reverse traversal from each pixel's last contributor,
 //                    recomputing T_i = T_{i+1} / (1 - alpha_i); per-Gaussian
-//                    2D gradients are reduced across the warp with shuffles and
-//                    added with one atomic per (warp, Gaussian, field).
+//                    a warp's per-lane 2D gradient sums of three splats are
+//                    summed row-wise through shared memory and added with one
+//                    atomic per (warp, Gaussian, field).
 //  k_preprocess_bwd  chain rule to the 59 parameters.
 //  k_adam            masked Adam (App. A.1, Eq. masked_update).
 #include <math.h>
@@ -204,7 +205,17 @@ struct PPOut {
   int* radius;
   uint32_t* ntiles;
   uint32_t* vflag;
+  int32_t* tdiff = nullptr;  // tile difference array and visible count of the tile binning (may be null)
+  uint32_t* nvis = nullptr;
 };
+
+// One distinct corner of a warp's tile rects: the lanes naming the same cell
+// add their +-1 with one atomic.
+__device__ __forceinline__ void corner_add(int32_t* __restrict__ d, int idx, int v) {
+  const uint32_t key = idx < 0 ? 0xffffffffu : (uint32_t)idx;
+  const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  if (idx >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d[idx], v * __popc(peers));
+}
 
 template <bool BF>
 __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam c, PPOut o, uint8_t* touched,
@@ -212,10 +223,11 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
   const unsigned item = blockIdx.x / cpi;
   const unsigned lane = (blockIdx.x - item * cpi) * PP_THREADS + threadIdx.x;
   const uint32_t B = rl.B;
-  if (lane >= B) return;
+  const bool inb = lane < B;  // no early return: the corner atomics below are warp-wide
   const uint64_t i = (uint64_t)item * B + lane;
   uint32_t area = 0;
-  if (lane < rl.item_count[item]) {
+  int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+  if (inb && lane < rl.item_count[item]) {
     const float* slot = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
     const float* p = slot + lane;
     const __nv_bfloat16* q16 = sh16(slot, B, lane);
@@ -228,10 +240,10 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
         float mid = 0.5f * (g.a + g.c);
         float lam1 = mid + sqrtf(fmaxf(0.1f, mid * mid - g.det));
         int r = (int)ceilf(3.f * sqrtf(lam1));
-        int x0 = min(max(floor_div_tile(k.u, -r), 0), c.TX);
-        int x1 = min(max(floor_div_tile(k.u, r) + 1, 0), c.TX);
-        int y0 = min(max(floor_div_tile(k.v, -r), 0), c.TY);
-        int y1 = min(max(floor_div_tile(k.v, r) + 1, 0), c.TY);
+        x0 = min(max(floor_div_tile(k.u, -r), 0), c.TX);
+        x1 = min(max(floor_div_tile(k.u, r) + 1, 0), c.TX);
+        y0 = min(max(floor_div_tile(k.v, -r), 0), c.TY);
+        y1 = min(max(floor_div_tile(k.v, r) + 1, 0), c.TY);
         if (x1 > x0 && y1 > y0) {
           area = (uint32_t)((x1 - x0) * (y1 - y0));
           // colour from the degree-3 SH at the view direction
@@ -259,8 +271,22 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
       }
     }
   }
-  o.ntiles[i] = area;
-  o.vflag[i] = area ? 1u : 0u;
+  if (inb) {
+    o.ntiles[i] = area;
+    o.vflag[i] = area ? 1u : 0u;
+  }
+  if (o.tdiff) {
+    // the rect [x0, x1) x [y0, y1) into the tile difference array
+    // ((TX + 1) x (TY + 1)), and the visible count
+    const int S = c.TX + 1;
+    const bool v = area != 0;
+    corner_add(o.tdiff, v ? y0 * S + x0 : -1, 1);
+    corner_add(o.tdiff, v ? y0 * S + x1 : -1, -1);
+    corner_add(o.tdiff, v ? y1 * S + x0 : -1, -1);
+    corner_add(o.tdiff, v ? y1 * S + x1 : -1, 1);
+    const uint32_t vb = __ballot_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && vb) atomicAdd(o.nvis, (uint32_t)__popc(vb));
+  }
 }
 
 __global__ void k_compact_visible(uint64_t V, const uint32_t* __restrict__ ntiles, const uint32_t* __restrict__ pos,
@@ -368,141 +394,6 @@ __global__ void __launch_bounds__(EP_THREADS) k_emit_pairs(const uint32_t* __res
     }
     __syncthreads();
   }
-}
-
-// List segments of the backward work split.  A tile whose list is longer
-// than R_SEG is composited backward as ceil(length / R_SEG) segments (at most
-// R_NSEG_MAX, the last one taking the rest), each an independent CTA; the
-// forward records per pixel (T, accumulated colour) at every segment boundary
-// and, in one more slot, (T_final, final colour).  One tile's backward is
-// otherwise a single CTA whose serial work can exceed the share of an SM slot
-// several times (the longest lists are a few percent of the tiles).
-constexpr int R_SEG = 256;  // a multiple of 32 (one staging batch)
-constexpr uint32_t R_NSEG_MAX = 255;
-__host__ __device__ __forceinline__ uint32_t seg_count(uint32_t len) {
-  const uint32_t n = (len + R_SEG - 1) / R_SEG;
-  return n <= 1 ? 1u : (n < R_NSEG_MAX ? n : R_NSEG_MAX);
-}
-
-// Tile order of the raster launches, longest pair list first (so the long
-// tiles do not start last), in one CTA: a stable counting sort of the tiles on
-// a logarithmic length bucket (255 - 16 log2(1 + length), clamped to 0..255);
-// the order is a scheduling heuristic, so bucket ties keep tile order.  Then,
-// in that order, the checkpoint slots of the split tiles (while they fit in
-// ck_cap) and the backward units (tile | segment << 24), their count in
-// *n_units.
-constexpr int TO_THREADS = 1024;
-__device__ __forceinline__ uint32_t to_block_scan(uint32_t x, uint32_t* sw, uint32_t& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) sw[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const uint32_t v = sw[lane];  // TO_THREADS / 32 == 32 warps
-    uint32_t vi = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
-      if (lane >= o) vi += y;
-    }
-    sw[lane] = vi - v;
-    if (lane == 31) sw[32] = vi;
-  }
-  __syncthreads();
-  const uint32_t r = sw[w] + inc - x;
-  total = sw[32];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(TO_THREADS) k_tile_order(const uint2* __restrict__ ranges, uint32_t tiles,
-                                                          uint32_t* __restrict__ order, uint32_t* __restrict__ tck,
-                                                          uint32_t* __restrict__ units,
-                                                          uint32_t* __restrict__ n_units, uint32_t ck_cap) {
-  __shared__ uint32_t cnt[32][256];
-  __shared__ uint32_t base[256];
-  __shared__ uint32_t sw[33];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int e = tid; e < 32 * 256; e += TO_THREADS) (&cnt[0][0])[e] = 0;
-  __syncthreads();
-  // warp w owns the tiles [w * per, (w + 1) * per), 32 at a time
-  const uint32_t per = ((tiles + 31) / 32 + 31) / 32 * 32;
-  const uint32_t t_lo = w * per, t_hi = min(tiles, t_lo + per);
-  auto bucket = [&](uint32_t t) {
-    const uint2 r = ranges[t];
-    const float l = log2f(1.f + (float)(r.y - r.x));
-    const int b = 255 - (int)(16.f * l);
-    return (uint32_t)(b < 0 ? 0 : b);
-  };
-  for (uint32_t t0 = t_lo; t0 < t_hi; t0 += 32)
-    if (t0 + lane < t_hi) atomicAdd(&cnt[w][bucket(t0 + lane)], 1u);
-  __syncthreads();
-  if (tid < 256) {
-    uint32_t run = 0;
-    for (int k = 0; k < 32; ++k) {
-      const uint32_t c = cnt[k][tid];
-      cnt[k][tid] = run;
-      run += c;
-    }
-    base[tid] = run;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < 256; ++b) {
-      const uint32_t c = base[b];
-      base[b] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t t0 = t_lo; t0 < t_hi; t0 += 32) {
-    const uint32_t t = t0 + lane;
-    const bool ok = t < t_hi;
-    const uint32_t b = ok ? bucket(t) : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    const int leader = __ffs(peers) - 1;
-    uint32_t o = 0;
-    if (lane == leader && ok) {
-      o = cnt[w][b];
-      cnt[w][b] = o + __popc(peers);
-    }
-    o = __shfl_sync(0xffffffffu, o, leader);
-    if (ok) order[base[b] + o + __popc(peers & lt)] = t;
-    __syncwarp();
-  }
-  if (!units) return;
-  __syncthreads();  // order[] is read back below by other threads of the CTA
-  uint32_t ccarry = 0, ucarry = 0;
-  for (uint32_t i0 = 0; i0 < tiles; i0 += TO_THREADS) {
-    const uint32_t i = i0 + tid;
-    uint32_t t = 0, ns = 1;
-    if (i < tiles) {
-      t = order[i];
-      const uint2 r = ranges[t];
-      ns = seg_count(r.y - r.x);
-    }
-    // a split tile takes ns slots: ns - 1 boundaries and its final state
-    const uint32_t want = ns > 1 ? ns : 0u;
-    uint32_t ctot, utot;
-    const uint32_t cb = ccarry + to_block_scan(want, sw, ctot);
-    const bool split = want > 0 && cb + want <= ck_cap;
-    const uint32_t nu = i < tiles ? (split ? ns : 1u) : 0u;
-    const uint32_t ub = ucarry + to_block_scan(nu, sw, utot);
-    if (i < tiles) {
-      tck[t] = split ? cb : ~0u;
-      for (uint32_t g = 0; g < nu; ++g) units[ub + g] = t | (g << 24);
-    }
-    ccarry += ctot;
-    ucarry += utot;
-  }
-  if (tid == 0) *n_units = ucarry;
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ np_dev, uint64_t cap, const uint32_t* __restrict__ pkeys,
@@ -723,10 +614,58 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) k_raster_fwd(const uint2* __re
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Backward partials: a warp's per-lane sums for a splat wait in shared
+// memory until RB_SLOTS splats are pending; then lane r adds up row r (the 32
+// lanes' values of one field of one splat) and adds the field's gradient with
+// one atomic.  Rows are padded to RB_ROW floats so that the 16-byte reads of
+// eight lanes fall in distinct bank groups.
+constexpr int RB_SLOTS = 3;  // 27 rows: one row per lane
+constexpr int RB_ROW = 36;
+
+// Sums the rows of nslot pending splats and adds their 2D gradients: fields
+// u, v (A sx + B sy and B sx + C sy of the geometric sums), the conic
+// (-1/2, -1, -1/2 times the second moments), opacity and colour.
+__device__ __forceinline__ void flush_partials(float (*red)[RB_ROW], const float4* rinfo, int nslot, int lane,
+                                               float* __restrict__ g2, uint64_t V) {
+  __syncwarp();  // every lane's row entries are written
+  const bool mine = lane < 9 * nslot;
+  float s = 0.f;
+  if (mine) {
+    const float4* r4 = reinterpret_cast<const float4*>(red[lane]);
+    float4 x[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+    for (int i = 0; i < 8; ++i) x[i] = r4[i];
+#pragma unroll
+    for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+      for (int i = 0; i < w; ++i) {
+        x[i].x += x[i + w].x;
+        x[i].y += x[i + w].y;
+        x[i].z += x[i + w].z;
+        x[i].w += x[i + w].w;
+      }
+    s = (x[0].x + x[0].y) + (x[0].z + x[0].w);
+  }
+  // the position fields combine the two first-moment sums of their splat
+  const float up = __shfl_down_sync(0xffffffffu, s, 1);
+  const float dn = __shfl_up_sync(0xffffffffu, s, 1);
+  if (mine) {
+    const int slot = lane / 9, f = lane - 9 * slot;
+    const float4 in = rinfo[slot];  // A, B, C, Gaussian id
+    float fin;
+    if (f == 0)
+      fin = in.x * s + in.y * up;
+    else if (f == 1)
+      fin = in.z * s + in.y * dn;
+    else if (f == 3)
+      fin = -s;
+    else if (f == 2 || f == 4)
+      fin = -0.5f * s;
+    else
+      fin = s;
+    if (fin != 0.f) atomicAdd(&g2[(uint64_t)f * V + __float_as_uint(in.w)], fin);
+  }
+  __syncwarp();  // the rows are rewritten after the flush
 }
 
 __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restrict__ ranges,
@@ -742,6 +681,8 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
                                                          const uint32_t* __restrict__ tck,
                                                          const float4* __restrict__ ck) {
   __shared__ Splat s_sp[R_WARPS][32];
+  __shared__ __align__(16) float s_red[R_WARPS][9 * RB_SLOTS][RB_ROW];
+  __shared__ float4 s_rinfo[R_WARPS][RB_SLOTS];
   // the CTA's unit: one tile, or one list segment [b0, b1) of a split tile
   int tile = (int)blockIdx.x, seg = 0;
   if (units) {
@@ -803,14 +744,12 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
     }
     wlast = b1;
   }
-  // reduce-scatter roles: lane l ends with the warp sum of value
-  // 4 bit4(l) + 2 bit3(l) + bit2(l) of v[0..7]; v[8] by butterfly
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-  const int qsel = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
-  // the lane's final value, branch-free: b1 (cA A + cC C + cK) + other cB B
-  // (sum 0: A sx + B sy; sum 1: B sx + C sy; conic sums: -1/2, -1, -1/2)
-  const float cA = qsel == 0 ? 1.f : 0.f, cC = qsel == 1 ? 1.f : 0.f, cB = qsel < 2 ? 1.f : 0.f;
-  const float cK = qsel < 2 ? 0.f : (qsel == 3 ? -1.f : (qsel == 2 || qsel == 4 ? -0.5f : 1.f));
+  // the lane-wise partials of up to RB_SLOTS contributing splats wait in
+  // shared memory (row 9 s + f of slot s, field f); a flush sums each row
+  // (lane r sums row r) and adds it with one atomic
+  float(*red)[RB_ROW] = s_red[wid];
+  float4* rinfo = s_rinfo[wid];
+  int nslot = 0;
   for (int top = wlast; top > b0; top -= 32) {
     // lane l stages list position top - 1 - l: ascending lanes, descending positions
     const int k0 = top - 1 - lane;
@@ -824,7 +763,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       const float4 a = sp[j].a;
       const float4 bb = sp[j].b;
       const float cb = sp[j].c;
-      // v: sums over the warp's pixels of dpw dx, dpw dy, dpw dx^2, dpw dx dy,
+      // v: sums over the thread's pixels of dpw dx, dpw dy, dpw dx^2, dpw dx dy,
       // dpw dy^2 (dpw = dL/dpower; the conic and constant factors are applied
       // after the reduction), dL/dopacity-activation, dL/d(r, g, b)
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -865,39 +804,18 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         v[4] += dpw * dyy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
-        float b4[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float keep = h4 ? v[4 + t] : v[t];
-          const float send = h4 ? v[t] : v[4 + t];
-          b4[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-        float b2[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const float keep = h3 ? b4[2 + t] : b4[t];
-          const float send = h3 ? b4[t] : b4[2 + t];
-          b2[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-        float b1 = (h2 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b2[0] : b2[1], 4);
-        b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
-        b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
-        const float s8 = warp_sum(v[8]);
-        // d power / du = A dx + B dy, d power / dv = B dx + C dy: the lanes of
-        // sums 0 and 1 (lanes l and l ^ 4) swap their sums; conic gradients
-        // carry the factors -1/2, -1, -1/2
-        const float other = __shfl_xor_sync(0xffffffffu, b1, 4);
-        const float fin = b1 * (cA * a.z + cC * bb.x + cK) + other * (cB * a.w);
-        const uint32_t id = sp[j].id;
-        if ((lane & 3) == 0) {
-          if (fin != 0.f) atomicAdd(&g2[(uint64_t)qsel * V + id], fin);
-        } else if (lane == 1 && s8 != 0.f) {
-          atomicAdd(&g2[8ull * V + id], s8);
+        for (int f = 0; f < 9; ++f) red[9 * nslot + f][lane] = v[f];
+        if (lane == 0) rinfo[nslot] = make_float4(a.z, a.w, bb.x, __uint_as_float(sp[j].id));
+        if (++nslot == RB_SLOTS) {
+          flush_partials(red, rinfo, nslot, lane, g2, V);
+          nslot = 0;
         }
       }
     }
     __syncwarp();  // the batch slots are rewritten next
   }
+  if (nslot) flush_partials(red, rinfo, nslot, lane, g2, V);
 }
 
 // Chain rule of the Level-2 preprocess (exact derivative of k_preprocess)
@@ -1631,11 +1549,18 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.ranges, cs.cap_tiles * sizeof(uint2)));
   TGS_CUDA(cudaMalloc(&cs.t_final, cs.cap_pix * sizeof(float)));
   TGS_CUDA(cudaMalloc(&cs.n_last, cs.cap_pix * sizeof(int)));
-  TGS_CUDA(cudaMalloc(&cs.counters, 8 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.counters, 16 * sizeof(uint32_t)));
   TGS_CUDA(cudaMallocHost(&cs.counters_host, 8 * sizeof(uint32_t)));
-  TGS_CUDA(cudaMalloc(&cs.bin_ctl, BIN_CTL_WORDS * sizeof(uint32_t)));
-  TGS_CUDA(cudaMalloc(&cs.status1, bin_status1_words(V) * sizeof(uint64_t)));
-  TGS_CUDA(cudaMemset(cs.status1, 0, bin_status1_words(V) * sizeof(uint64_t)));
+  {
+    const int mtx = (max_w + TILE - 1) / TILE, mty = (max_h + TILE - 1) / TILE;
+    const size_t tb = tile_scan_smem_bytes(mtx, mty);
+    TGS_CHECK(tb <= TILE_SCAN_SMEM_MAX, TGS_ERR_INVALID,
+              "image too large for the tile binning (at most 40,960 cells of (tiles_x + 1) x (tiles_y + 1))");
+    TGS_CUDA(cudaMalloc(&cs.tdiff, tb));
+    TGS_CUDA(cudaMemset(cs.tdiff, 0, tb));
+  }
+  TGS_CUDA(cudaMalloc(&cs.tfill, cs.cap_tiles * sizeof(uint32_t)));
+  TGS_CUDA(cudaMalloc(&cs.tbig, cs.cap_tiles * sizeof(uint32_t)));
   TGS_CUDA(cudaMalloc(&cs.torder, 2 * cs.cap_tiles * sizeof(uint32_t)));
   // backward split: up to 4 checkpoint slots per tile, at most 8192 (32 MB)
   TGS_CHECK(cs.cap_tiles < (1ull << 24), TGS_ERR_INVALID, "image has too many tiles");
@@ -1644,7 +1569,7 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.tck, cs.cap_tiles * sizeof(uint32_t)));
   TGS_CUDA(cudaMalloc(&cs.units, (cs.cap_tiles + cs.ck_cap) * sizeof(uint32_t)));
   TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_counts, cudaEventDisableTiming));
-  TGS_CUDA(cudaMemset(cs.counters, 0, 8 * sizeof(uint32_t)));
+  TGS_CUDA(cudaMemset(cs.counters, 0, 16 * sizeof(uint32_t)));
   cs.cap_pairs = 0;
   cam_state_grow_pairs(cs, cap_pairs > 0 ? cap_pairs : 1024, 0);
 }
@@ -1662,15 +1587,6 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
     cs.cap_pairs = cap;
     want = cap > cs.cap_v ? cap : cs.cap_v;
   }
-  const uint64_t sw = bin_status_words(cs.cap_v, cs.cap_pairs);
-  if (sw > cs.status_words) {
-    if (s) TGS_CUDA(cudaStreamSynchronize(s));
-    if (cs.status) TGS_CUDA(cudaFree(cs.status));
-    TGS_CUDA(cudaMalloc(&cs.status, sw * sizeof(uint64_t)));
-    // zero: no stale word carries a live epoch (epochs start at 1)
-    TGS_CUDA(cudaMemset(cs.status, 0, sw * sizeof(uint64_t)));
-    cs.status_words = sw;
-  }
   size_t sb = radix_scratch_bytes(want);
   size_t sc = scan_scratch_bytes(want);
   if (sc > sb) sb = sc;
@@ -1686,7 +1602,7 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
 void cam_state_free(CamState& cs) {
   void* ptrs[] = {cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.dkeys,
                   cs.dvals, cs.g2, cs.ranges, cs.t_final, cs.n_last, cs.counters, cs.pkeys, cs.pvals, cs.scratch,
-                  cs.torder, cs.ck, cs.tck, cs.units, cs.bin_ctl, cs.status, cs.status1};
+                  cs.torder, cs.ck, cs.tck, cs.units, cs.tdiff, cs.tfill, cs.tbig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (cs.counters_host) cudaFreeHost(cs.counters_host);
@@ -1709,12 +1625,11 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
   const uint64_t tiles = (uint64_t)cam.TX * cam.TY;
   const float3 bg3 = make_float3(bg[0], bg[1], bg[2]);
   uint32_t* nv_dev = cs.counters;      // visible Gaussians
-  uint32_t* np_dev = cs.counters + 1;  // pairs (before the capacity clamp)
   TGS_CUDA(cudaMemsetAsync(cs.ranges, 0, tiles * sizeof(uint2), s));
   TGS_CUDA(cudaMemsetAsync(cs.counters, 0, 2 * sizeof(uint32_t), s));  // the overflow words stay
   if (V > 0) {
     unsigned cpi = div_up(rl.B, PP_THREADS);
-    PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan};
+    PPOut o{cs.xy, cs.depth, cs.conic_o, cs.rgb, cs.rect, cs.radius, cs.ntiles, cs.scan, cs.tdiff, nv_dev};
     tm->begin(StageTimer::PRE, s);
     if (rl.bf16)
       k_preprocess<true><<<rl.n_items * cpi, PP_THREADS, 0, s>>>(rl, cam, o, touched, item_touched, cpi);
@@ -1724,10 +1639,7 @@ void render_forward(const RenderList& rl, const DevCam& cam, const float bg[3], 
     tm->end(StageTimer::PRE, s);
     tm->begin(StageTimer::SORT, s);
     // the sizes stay on the device: no host round trip inside a render
-    bin_and_sort(V, cam.TX, tiles, cs, s);
-    k_tile_order<<<1, TO_THREADS, 0, s>>>(cs.ranges, (uint32_t)tiles, cs.torder, cs.tck, cs.units,
-                                          cs.counters + 5, cs.ck_cap);
-    TGS_LAUNCHED();
+    bin_tiles(V, cam.TX, cam.TY, cs, s);
     cs.order_valid = true;
     tm->end(StageTimer::SORT, s);
   } else {
@@ -1755,8 +1667,8 @@ bool cam_state_counts(CamState& cs, bool wait) {
       if (e == cudaErrorNotReady) return false;
       TGS_CUDA(e);
     }
-    TGS_CHECK(cs.counters_host[6] == 0, TGS_ERR_TIMEOUT,
-              "a binning look-back wait ran out (its partition's predecessor never published)");
+    TGS_CHECK(cs.counters_host[6] == 0, TGS_ERR_STATE,
+              "tile binning: a tile received more pairs than its rect count");
     cs.n_vis = cs.counters_host[0];
     cs.n_pairs = cs.counters_host[1];
     cs.overflow = cs.counters_host[2] != 0;

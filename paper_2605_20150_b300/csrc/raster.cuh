@@ -34,6 +34,20 @@ struct RenderList {
   uint64_t capacity() const { return (uint64_t)n_items * B; }
 };
 
+// List segments of the backward work split.  A tile whose list is longer
+// than R_SEG is composited backward as ceil(length / R_SEG) segments (at most
+// R_NSEG_MAX, the last one taking the rest), each an independent CTA; the
+// forward records per pixel (T, accumulated colour) at every segment boundary
+// and, in one more slot, (T_final, final colour).  One tile's backward is
+// otherwise a single CTA whose serial work can exceed the share of an SM slot
+// several times (the longest lists are a few percent of the tiles).
+constexpr int R_SEG = 256;  // a multiple of 32 (one staging batch)
+constexpr uint32_t R_NSEG_MAX = 255;
+__host__ __device__ __forceinline__ uint32_t seg_count(uint32_t len) {
+  const uint32_t n = (len + R_SEG - 1) / R_SEG;
+  return n <= 1 ? 1u : (n < R_NSEG_MAX ? n : R_NSEG_MAX);
+}
+
 // Per-camera state of one render (capacities fixed at allocation).
 struct CamState {
   uint64_t cap_v = 0, cap_pairs = 0, cap_pix = 0, cap_tiles = 0;
@@ -55,6 +69,9 @@ struct CamState {
   uint32_t* pvals = nullptr;
   // per tile / pixel
   uint2* ranges = nullptr;
+  int32_t* tdiff = nullptr;    // (max TX + 1) x (max TY + 1) tile difference array, zero between renders
+  uint32_t* tfill = nullptr;   // cap_tiles: pairs placed per tile
+  uint32_t* tbig = nullptr;    // cap_tiles: tiles sorted by the large-tile sort
   uint32_t* torder = nullptr;  // 2 x cap_tiles: tiles, longest pair list first
   bool order_valid = false;
   // backward work split: a tile with a long list is composited backward as
@@ -69,16 +86,10 @@ struct CamState {
   // scratch for scans and sorts
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  uint32_t* counters = nullptr;  // device [8]: n_vis, n_pairs (before the clamp), overflow, pairs needed, -,
-                                 // backward units, binning look-back timeout
+  uint32_t* counters = nullptr;  // device [16]: n_vis, n_pairs (before the clamp), overflow, pairs needed, -,
+                                 // backward units, binning consistency error, -, then the tile
+                                 // binning's words (this render's overflow, long-list counts)
   uint32_t* counters_host = nullptr;  // pinned mirror (8 words), copied at the end of each render
-  // binning (bin.cu): control words (digit counts and tickets, cleared per
-  // render), look-back status words tagged with a per-launch epoch
-  uint32_t* bin_ctl = nullptr;
-  uint64_t* status = nullptr;   // per-digit partition status of the radix passes
-  uint64_t* status1 = nullptr;  // partition status of compaction and pair emission
-  uint64_t status_words = 0;
-  uint32_t epoch = 0;
   cudaEvent_t ev_counts = nullptr;    // recorded after that copy
   uint32_t* step_flag = nullptr;      // optional device word raised with the overflow flag
   // results of the last render (valid after cam_state_counts)
@@ -90,23 +101,24 @@ struct CamState {
 
 void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w, int max_h);
 
-// Binning (bin.cu): digit-count and ticket words of one render, and the
-// look-back status words the binning kernels need for the given capacities.
-constexpr uint64_t BIN_CTL_WORDS = 8 * 256 + 16;
-uint64_t bin_status_words(uint64_t cap_v, uint64_t cap_pairs);
-uint64_t bin_status1_words(uint64_t cap_v);
-// Visible compaction, depth sort, pair emission, tile sort and tile ranges of
-// a render whose preprocess has run (V render-list positions, TX x (tiles /
-// TX) tiles); the counts stay on the device (cs.counters).
-void bin_and_sort(uint64_t V, int TX, uint64_t tiles, CamState& cs, cudaStream_t s);
+// Tile binning (tiles.cu) of a render whose preprocess has run with the
+// tile difference array (V render-list positions, TX x TY tiles): per-tile
+// counts and ranges, pair emission, per-tile depth order, the tile order of
+// the raster launches and the backward units.  The counts stay on the device
+// (cs.counters).  The tile scan holds the (TX + 1) x (TY + 1) difference
+// array in shared memory, which bounds the image to TILE_SCAN_SMEM_MAX bytes
+// of it (40,960 cells: 3840 x 2160 uses 32,776).
+constexpr size_t TILE_SCAN_SMEM_MAX = 160 * 1024;
+size_t tile_scan_smem_bytes(int TX, int TY);
+void bin_tiles(uint64_t V, int TX, int TY, CamState& cs, cudaStream_t s);
 void cam_state_free(CamState& cs);
 void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s);
 // Reads the last render's counts into n_vis / n_pairs / overflow; wait =
 // false returns false if they have not reached the host yet.
 bool cam_state_counts(CamState& cs, bool wait);
 
-// Forward: preprocess -> visible compaction -> depth sort -> pair emission ->
-// tile sort -> ranges -> compositing.  touched (render-list bytes, may be
+// Forward: preprocess -> tile binning (counts, ranges, pair emission,
+// per-tile depth sort) -> compositing.  touched (render-list bytes, may be
 // null) gets 1 for visible Gaussians; item_touched (per item, may be null)
 // gets 1 for items with a visible Gaussian.  No host synchronisation: the
 // visible and pair counts stay on the device, pairs beyond cs.cap_pairs are
