@@ -604,11 +604,22 @@ int64_t orc_bin_sort(int64_t n, const double* S, int W, int H, int phantom, uint
 /* nlast = 1 + position (within the tile list) of the last included entry.   */
 /* img: H x W x 3.  Slack (test support): a bound on how far a result taken   */
 /* with any of the valid outcomes of a borderline decision can move the       */
-/* pixel: every entry whose alpha or stop test lies within a relative tol_a   */
-/* of its threshold, or whose Gaussian is 'border', or any phantom entry      */
+/* pixel.  An FP32 alpha carries a relative error of about e_a = 1e-6 +     */
+/* POWER_REL_ERR |power| (the power is a quadratic form of FP32 centre and    */
+/* conic values, so its absolute error grows with |power|; 1e-6 for the      */
+/* exponential).  Every entry whose alpha test lies within max(tol_a, e_a)   */
+/* (relative) of 1/255, or whose Gaussian is 'border', or any phantom entry  */
 /* (ph_* lists: border Gaussians over their one-tile-enlarged rect), adds    */
-/* 2 * alpha * T * max(rgb, bg).                                              */
+/* 2 * alpha * T * max(rgb, bg).  The stop test compares a product of        */
+/* (1 - alpha) factors, each with a relative error of alpha / (1 - alpha) e_a */
+/* plus two roundings: it is borderline when T' lies within the summed bound */
+/* eT (at least tol_a) of 1e-4, and either outcome there moves the pixel by  */
+/* at most T * max(rgb, bg) (the transmittance left), so the slack adds      */
+/* 2 * T * max(rgb, bg).                                                      */
 /* ------------------------------------------------------------------------ */
+#define POWER_REL_ERR 1e-5       /* relative error of an FP32 power (quadratic form) */
+#define FACTOR_ROUND 1.2e-7      /* two FP32 roundings per (1 - alpha) factor */
+
 static double eval_alpha(const double* s, int px, int py, double* power_out) {
   double dx = (double)px - s[0], dy = (double)py - s[1];
   double power = -0.5 * (s[3] * dx * dx + s[5] * dy * dy) - s[4] * dx * dy;
@@ -631,7 +642,7 @@ void orc_composite_fwd(int64_t n, const double* S, int W, int H, const uint32_t*
       int tile = (py / TILE) * TX + (px / TILE);
       uint32_t a = ranges[2 * tile], b = ranges[2 * tile + 1];
       uint32_t pa = ph_ranges ? ph_ranges[2 * tile] : 0, pb = ph_ranges ? ph_ranges[2 * tile + 1] : 0;
-      double T = 1.0, C[3] = {0, 0, 0}, sl = 0.0;
+      double T = 1.0, C[3] = {0, 0, 0}, sl = 0.0, eT = 0.0;
       int32_t last = 0;
       int done = 0;
       uint32_t j = a, q = pa;
@@ -665,15 +676,18 @@ void orc_composite_fwd(int64_t n, const double* S, int W, int H, const uint32_t*
         int border = s[19] != 0;
         if (al >= 0) {
           double Tn = T * (1.0 - al);
+          double ea = 1e-6 + POWER_REL_ERR * fabs(pw);
+          double eTn = eT + FACTOR_ROUND + al / (1.0 - al) * ea;
           if (border && al >= ALPHA_MIN * (1.0 - tol_a)) sl += 2.0 * al * T * cm;
-          else if (fabs(al - ALPHA_MIN) < tol_a * ALPHA_MIN) sl += 2.0 * al * T * cm;
-          else if (fabs(Tn - T_STOP) < tol_a * T_STOP) sl += 2.0 * al * T * cm;
+          else if (fabs(al - ALPHA_MIN) < fmax(tol_a, ea) * ALPHA_MIN) sl += 2.0 * al * T * cm;
+          else if (al >= ALPHA_MIN && fabs(Tn - T_STOP) < fmax(tol_a, eTn) * T_STOP) sl += 2.0 * T * cm;
           if (al >= ALPHA_MIN) {
             if (Tn < T_STOP) {
               done = 1;
             } else {
               for (int ch = 0; ch < 3; ++ch) C[ch] += s[7 + ch] * al * T;
               T = Tn;
+              eT = eTn;
               last = (int32_t)(j - a + 1);
             }
           }
