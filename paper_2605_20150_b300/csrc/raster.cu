@@ -280,12 +280,14 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess(RenderList rl, DevCam
     // ((TX + 1) x (TY + 1)), and the visible count
     const int S = c.TX + 1;
     const bool v = area != 0;
-    corner_add(o.tdiff, v ? y0 * S + x0 : -1, 1);
-    corner_add(o.tdiff, v ? y0 * S + x1 : -1, -1);
-    corner_add(o.tdiff, v ? y1 * S + x0 : -1, -1);
-    corner_add(o.tdiff, v ? y1 * S + x1 : -1, 1);
     const uint32_t vb = __ballot_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0 && vb) atomicAdd(o.nvis, (uint32_t)__popc(vb));
+    if (vb) {  // uniform
+      corner_add(o.tdiff, v ? y0 * S + x0 : -1, 1);
+      corner_add(o.tdiff, v ? y0 * S + x1 : -1, -1);
+      corner_add(o.tdiff, v ? y1 * S + x0 : -1, -1);
+      corner_add(o.tdiff, v ? y1 * S + x1 : -1, 1);
+      if ((threadIdx.x & 31) == 0) atomicAdd(o.nvis, (uint32_t)__popc(vb));
+    }
   }
 }
 
@@ -483,13 +485,21 @@ __device__ __forceinline__ bool splat_hits(const WarpPix& q, float x, float y, f
   return m <= 2.004f * L + 1e-3f;
 }
 
-// One splat as staged in shared memory.
+// One splat as staged in shared memory, with the conic folded into the
+// power's coefficients: power = dx (a2 dx + b2 dy) + c2 dy^2 with a2 = -A/2,
+// b2 = -B, c2 = -C/2 (exact scalings), evaluated as
+//   power = fma(dx, fma(b2, dy, a2 dx), c2 (dy dy))
+// by the forward and the backward alike, so both take the same alphas.
 struct Splat {
-  float4 a;  // x, y, A, B
-  float4 b;  // C, opacity, r, g
+  float4 a;  // x, y, a2, b2
+  float4 b;  // c2, opacity, r, g
   float c;   // b
   uint32_t id;
 };
+
+__device__ __forceinline__ float splat_power(float a2dx, float b2, float c2, float dx, float dy, float dyy) {
+  return __fmaf_rn(dx, __fmaf_rn(b2, dy, a2dx), __fmul_rn(c2, dyy));
+}
 
 __device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, const float2* __restrict__ xy,
                                             const float4* __restrict__ conic_o, const float4* __restrict__ rgb,
@@ -498,8 +508,8 @@ __device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, 
   const float2 g = xy[id];
   const float4 co = conic_o[id];
   const float4 cc = rgb[id];
-  slot->a = make_float4(g.x, g.y, co.x, co.y);
-  slot->b = make_float4(co.z, co.w, cc.x, cc.y);
+  slot->a = make_float4(g.x, g.y, -0.5f * co.x, -co.y);
+  slot->b = make_float4(-0.5f * co.z, co.w, cc.x, cc.y);
   slot->c = cc.z;
   slot->id = id;
   return splat_hits(q, g.x, g.y, co.x, co.y, co.z, co.w);
@@ -559,15 +569,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) k_raster_fwd(const uint2* __re
       const float4 bb = sp[j].b;
       const float cb = sp[j].c;
       act = false;
-      // the thread's pixels share their column: dx and A dx^2 once (the same
-      // correctly rounded operations as splat_power)
+      // the thread's pixels share their column: dx and a2 dx once
       const float dx = __fsub_rn(fpx, a.x);
-      const float adxx = __fmul_rn(a.z, __fmul_rn(dx, dx));
+      const float a2dx = __fmul_rn(a.z, dx);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const float dy = __fsub_rn((float)(q.py0 + k), a.y);
-        const float qf = __fadd_rn(adxx, __fmul_rn(bb.x, __fmul_rn(dy, dy)));
-        const float power = __fsub_rn(__fmul_rn(-0.5f, qf), __fmul_rn(a.w, __fmul_rn(dx, dy)));
+        const float power = splat_power(a2dx, a.w, bb.x, dx, dy, __fmul_rn(dy, dy));
         float G;
         const float alpha = splat_alpha(bb.y, power, G);
         const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
@@ -770,14 +778,13 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       bool contrib = false;
       const float dx = __fsub_rn(fpx, a.x);
       const float dxx = __fmul_rn(dx, dx);
-      const float adxx = __fmul_rn(a.z, dxx);
+      const float a2dx = __fmul_rn(a.z, dx);
 #pragma unroll
       for (int k = 0; k < R_PPT; ++k) {
         const float dy = __fsub_rn((float)(q.py0 + k), a.y);
         const float dyy = __fmul_rn(dy, dy);
         const float dxy = __fmul_rn(dx, dy);
-        const float qf = __fadd_rn(adxx, __fmul_rn(bb.x, dyy));
-        const float power = __fsub_rn(__fmul_rn(-0.5f, qf), __fmul_rn(a.w, dxy));
+        const float power = splat_power(a2dx, a.w, bb.x, dx, dy, dyy);
         float G;
         const float alpha = splat_alpha(bb.y, power, G);
         const bool ok = pos < last[k] && power <= 0.f && alpha >= ALPHA_MIN;
@@ -806,7 +813,8 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       if (__ballot_sync(0xffffffffu, contrib)) {
 #pragma unroll
         for (int f = 0; f < 9; ++f) red[9 * nslot + f][lane] = v[f];
-        if (lane == 0) rinfo[nslot] = make_float4(a.z, a.w, bb.x, __uint_as_float(sp[j].id));
+        // the conic (A, B, C) back from the staged coefficients (exact)
+        if (lane == 0) rinfo[nslot] = make_float4(-2.f * a.z, -a.w, -2.f * bb.x, __uint_as_float(sp[j].id));
         if (++nslot == RB_SLOTS) {
           flush_partials(red, rinfo, nslot, lane, g2, V);
           nslot = 0;
@@ -1569,6 +1577,13 @@ void cam_state_alloc(CamState& cs, uint64_t cap_v, uint64_t cap_pairs, int max_w
   TGS_CUDA(cudaMalloc(&cs.tck, cs.cap_tiles * sizeof(uint32_t)));
   TGS_CUDA(cudaMalloc(&cs.units, (cs.cap_tiles + cs.ck_cap) * sizeof(uint32_t)));
   TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_counts, cudaEventDisableTiming));
+  {
+    int lo = 0, hi = 0;
+    TGS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    TGS_CUDA(cudaStreamCreateWithPriority(&cs.aux, cudaStreamNonBlocking, hi));
+    TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_fork, cudaEventDisableTiming));
+    TGS_CUDA(cudaEventCreateWithFlags(&cs.ev_join, cudaEventDisableTiming));
+  }
   TGS_CUDA(cudaMemset(cs.counters, 0, 16 * sizeof(uint32_t)));
   cs.cap_pairs = 0;
   cam_state_grow_pairs(cs, cap_pairs > 0 ? cap_pairs : 1024, 0);
@@ -1607,6 +1622,9 @@ void cam_state_free(CamState& cs) {
     if (p) cudaFree(p);
   if (cs.counters_host) cudaFreeHost(cs.counters_host);
   if (cs.ev_counts) cudaEventDestroy(cs.ev_counts);
+  if (cs.ev_fork) cudaEventDestroy(cs.ev_fork);
+  if (cs.ev_join) cudaEventDestroy(cs.ev_join);
+  if (cs.aux) cudaStreamDestroy(cs.aux);
   cs = CamState();
 }
 

@@ -91,6 +91,8 @@ struct CamState {
                                  // binning's words (this render's overflow, long-list counts)
   uint32_t* counters_host = nullptr;  // pinned mirror (8 words), copied at the end of each render
   cudaEvent_t ev_counts = nullptr;    // recorded after that copy
+  cudaStream_t aux = nullptr;         // the tile order's stream beside the binning (render_forward)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint32_t* step_flag = nullptr;      // optional device word raised with the overflow flag
   // results of the last render (valid after cam_state_counts)
   uint64_t n_vis = 0, n_pairs = 0, pairs_needed = 0;

@@ -35,7 +35,7 @@ constexpr int TS_THREADS = 1024;
 constexpr int EM_THREADS = 256;
 constexpr uint32_t EM_WARP = 32;    // tiles above which a Gaussian leaves the 32-position warps
 constexpr uint32_t EM_CTA = 1024;   // tiles above which a whole CTA (not one warp) emits a Gaussian
-constexpr int EM_UNROLL = 4;        // pairs per lane per round (their slot claims in flight together)
+constexpr int EM_UNROLL = 8;        // pairs per lane per round (their slot claims in flight together)
 constexpr int SORT_THREADS = 256;
 constexpr uint32_t SORT_SMALL = 8 * SORT_THREADS;  // 2048 keys: a small CTA (two 16 KB buffers)
 constexpr int SORT_BIG_THREADS = 1024;
@@ -86,23 +86,13 @@ __device__ __forceinline__ unsigned long long cta_excl64(unsigned long long x, u
 }
 
 // One CTA: per-tile counts from the difference array (which it leaves zero
-// for the next render), tile ranges, the overflow check, the list of long
-// tiles, and the raster tile order with the backward units.
-//
-// Tile order: a stable counting sort of the tiles on a logarithmic length
-// bucket (255 - 16 log2(1 + length), clamped at 0), so the longest lists
-// start first; it is a scheduling heuristic, so ties keep tile order.  Then,
-// in that order, split tiles take checkpoint slots (while they fit in ck_cap)
-// and the backward units (tile | segment << 24) are listed.
+// for the next render), tile ranges, the overflow check and the list of long
+// tiles.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(int32_t* __restrict__ tdiff, int TX, int TY, uint64_t cap,
                                                          uint32_t* __restrict__ counters, uint32_t* step_flag,
                                                          uint2* __restrict__ ranges, uint32_t* __restrict__ tfill,
-                                                         uint32_t* __restrict__ tbig, uint32_t* __restrict__ order,
-                                                         uint32_t* __restrict__ tck, uint32_t* __restrict__ units,
-                                                         uint32_t ck_cap) {
+                                                         uint32_t* __restrict__ tbig) {
   extern __shared__ int32_t Dm[];  // (TY + 1) x (TX + 1): difference array, then counts
-  __shared__ uint32_t cnt[32][256];
-  __shared__ uint32_t base[256];
   __shared__ unsigned long long sw[33];
   __shared__ uint32_t s_nbig;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -113,7 +103,6 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(int32_t* __restrict__ 
     Dm[e] = tdiff[e];
     tdiff[e] = 0;
   }
-  for (int e = tid; e < 32 * 256; e += TS_THREADS) (&cnt[0][0])[e] = 0;
   if (tid == 0) s_nbig = 0;
   __syncthreads();
   // integrate along rows (warp per row), then along columns (thread per column)
@@ -173,14 +162,39 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(int32_t* __restrict__ 
       o += c;
     }
   }
-  // tile order: warp w owns the tiles [w * tw, (w + 1) * tw)
+  __syncthreads();
+  if (tid == 0) counters[C_NBIG_T] = s_nbig;
+}
+
+// One CTA, on a stream of its own beside the emission and the sorts: the
+// raster tile order from the tile ranges (empty after an overflow).
+//
+// Tile order: a stable counting sort of the tiles on a logarithmic length
+// bucket (255 - 16 log2(1 + length), clamped at 0), so the longest lists
+// start first; it is a scheduling heuristic, so ties keep tile order.  Then,
+// in that order, split tiles take checkpoint slots (while they fit in ck_cap)
+// and the backward units (tile | segment << 24) are listed, their count in
+// counters[5].
+__global__ void __launch_bounds__(TS_THREADS) k_tile_order(const uint2* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ counters,
+                                                          uint32_t* __restrict__ order, uint32_t* __restrict__ tck,
+                                                          uint32_t* __restrict__ units, uint32_t ck_cap) {
+  __shared__ uint32_t cnt[32][256];
+  __shared__ uint32_t base[256];
+  __shared__ unsigned long long sw[33];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < 32 * 256; e += TS_THREADS) (&cnt[0][0])[e] = 0;
+  __syncthreads();
+  // warp w owns the tiles [w * tw, (w + 1) * tw)
   const uint32_t tw = ((tiles + 31) / 32 + 31) / 32 * 32;
   const uint32_t w_lo = min(tiles, (uint32_t)w * tw), w_hi = min(tiles, w_lo + tw);
-  auto len = [&](uint32_t t) { return over ? 0u : count(t); };
+  auto len = [&](uint32_t t) {
+    const uint2 r = ranges[t];
+    return r.y - r.x;
+  };
   for (uint32_t a = w_lo; a < w_hi; a += 32)
     if (a + lane < w_hi) atomicAdd(&cnt[w][bucket_of(len(a + lane))], 1u);
   __syncthreads();
-  if (tid == 0) counters[C_NBIG_T] = s_nbig;
   if (tid < 256) {
     uint32_t run = 0;
     for (int k = 0; k < 32; ++k) {
@@ -255,29 +269,43 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(int32_t* __restrict__ 
   if (tid == 0) counters[5] = (uint32_t)ucarry;
 }
 
-// Claims slots for up to 32 pairs of a warp (tile FULL: no pair) and writes
-// them: lanes placing a pair in the same tile claim with one atomic.
+// Claims slots for up to 32 EM_UNROLL pairs of a warp (tile FULL: no pair)
+// and writes them: lanes placing a pair in the same tile claim with one
+// atomic.  The tile ranges are read and every atomic of the round is issued
+// before the first result is used, so their latencies overlap.
+// nsub (uniform over the warp): the sub-rounds u < nsub that hold a pair; the
+// others are skipped whole.
 __device__ __forceinline__ void place_pairs(const uint32_t (&tile)[EM_UNROLL], const uint32_t (&dk)[EM_UNROLL],
-                                            const uint32_t (&id)[EM_UNROLL], const uint2* __restrict__ ranges,
-                                            uint32_t* __restrict__ tfill, uint32_t* __restrict__ pkeys,
-                                            uint32_t* __restrict__ pvals, uint32_t* __restrict__ err) {
+                                            const uint32_t (&id)[EM_UNROLL], int nsub,
+                                            const uint2* __restrict__ ranges, uint32_t* __restrict__ tfill,
+                                            uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                            uint32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t o[EM_UNROLL], rank[EM_UNROLL];
+  uint2 rg[EM_UNROLL];
+  uint32_t peers[EM_UNROLL], o[EM_UNROLL];
+  int leader[EM_UNROLL];
+#pragma unroll
+  for (int u = 0; u < EM_UNROLL; ++u) rg[u] = tile[u] != FULL ? ranges[tile[u]] : make_uint2(0u, 0u);
 #pragma unroll
   for (int u = 0; u < EM_UNROLL; ++u) {
-    const uint32_t peers = __match_any_sync(FULL, tile[u]);
-    const int leader = __ffs(peers) - 1;
-    o[u] = tile[u] != FULL && lane == leader ? atomicAdd(&tfill[tile[u]], (uint32_t)__popc(peers)) : 0u;
-    o[u] = __shfl_sync(FULL, o[u], leader);
-    rank[u] = __popc(peers & lt);
+    peers[u] = 0u;
+    leader[u] = 0;
+    if (u < nsub) {  // uniform
+      peers[u] = __match_any_sync(FULL, tile[u]);
+      leader[u] = __ffs(peers[u]) - 1;
+    }
   }
+#pragma unroll
+  for (int u = 0; u < EM_UNROLL; ++u)
+    o[u] = tile[u] != FULL && lane == leader[u] ? atomicAdd(&tfill[tile[u]], (uint32_t)__popc(peers[u])) : 0u;
+#pragma unroll
+  for (int u = 0; u < EM_UNROLL; ++u) o[u] = __shfl_sync(FULL, o[u], leader[u]);
 #pragma unroll
   for (int u = 0; u < EM_UNROLL; ++u) {
     if (tile[u] == FULL) continue;
-    const uint2 rg = ranges[tile[u]];
-    const uint32_t pos = rg.x + o[u] + rank[u];
-    if (pos < rg.y) {
+    const uint32_t pos = rg[u].x + o[u] + __popc(peers[u] & lt);
+    if (pos < rg[u].y) {
       pkeys[pos] = dk[u];
       pvals[pos] = id[u];
     } else {
@@ -302,16 +330,24 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit_tiles(uint64_t V, const uin
                                                           uint32_t* __restrict__ mid, uint32_t* __restrict__ counters) {
   if (counters[C_OVER]) return;  // uniform
   const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const uint64_t nw = ((uint64_t)gridDim.x * EM_THREADS) >> 5;
   for (uint64_t b = (((uint64_t)blockIdx.x * EM_THREADS + threadIdx.x) >> 5) * 32; b < V; b += nw * 32) {
     const uint64_t i = b + lane;
     uint32_t n = i < V ? ntiles[i] : 0u;
-    if (n > EM_CTA) {
-      big[atomicAdd(&counters[C_NBIG_G], 1u)] = (uint32_t)i;
-      n = 0;
-    } else if (n > EM_WARP) {
-      mid[atomicAdd(&counters[C_NMID_G], 1u)] = (uint32_t)i;
-      n = 0;
+    // the listed Gaussians, one append per warp and list
+    const uint32_t bb = __ballot_sync(FULL, n > EM_CTA), bm = __ballot_sync(FULL, n > EM_WARP && n <= EM_CTA);
+    if (bb | bm) {
+      uint32_t ob = 0, om = 0;
+      if (lane == 0) {
+        if (bb) ob = atomicAdd(&counters[C_NBIG_G], (uint32_t)__popc(bb));
+        if (bm) om = atomicAdd(&counters[C_NMID_G], (uint32_t)__popc(bm));
+      }
+      ob = __shfl_sync(FULL, ob, 0);
+      om = __shfl_sync(FULL, om, 0);
+      if ((bb >> lane) & 1u) big[ob + __popc(bb & lt)] = (uint32_t)i;
+      if ((bm >> lane) & 1u) mid[om + __popc(bm & lt)] = (uint32_t)i;
+      if (n > EM_WARP) n = 0;
     }
     uint32_t inc = n;
 #pragma unroll
@@ -352,7 +388,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit_tiles(uint64_t V, const uin
         const uint32_t loc = k - oex, dy = loc / wdt;
         tile[u] = k < tot ? (y0 + dy) * (uint32_t)TX + x0 + (loc - dy * wdt) : FULL;
       }
-      place_pairs(tile, kd, id, ranges, tfill, pkeys, pvals, &counters[6]);
+      place_pairs(tile, kd, id, (int)min((tot - k0 + 31) / 32, (uint32_t)EM_UNROLL), ranges, tfill, pkeys, pvals,
+                  &counters[6]);
     }
   }
 }
@@ -387,7 +424,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit_big(const uint32_t* __restr
         kd[u] = dk;
         id[u] = i;
       }
-      place_pairs(tile, kd, id, ranges, tfill, pkeys, pvals, &counters[6]);
+      place_pairs(tile, kd, id, EM_UNROLL, ranges, tfill, pkeys, pvals, &counters[6]);
     }
   }
   const uint32_t nw = (gridDim.x * EM_THREADS) >> 5;
@@ -406,7 +443,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit_big(const uint32_t* __restr
         kd[u] = dk;
         id[u] = i;
       }
-      place_pairs(tile, kd, id, ranges, tfill, pkeys, pvals, &counters[6]);
+      place_pairs(tile, kd, id, (int)min((n - k0 + 31) / 32, (uint32_t)EM_UNROLL), ranges, tfill, pkeys, pvals,
+                  &counters[6]);
     }
   }
 }
@@ -602,8 +640,17 @@ void bin_tiles(uint64_t V, int TX, int TY, CamState& cs, cudaStream_t s) {
   TGS_CHECK(dsm <= TILE_SCAN_SMEM_MAX, TGS_ERR_CAPACITY, "image has too many tiles for the tile scan");
   TGS_CHECK(cs.cap_pairs < 0x80000000ull, TGS_ERR_CAPACITY, "pair capacity above 2^31");
   k_tile_scan<<<1, TS_THREADS, dsm, s>>>(cs.tdiff, TX, TY, cs.cap_pairs, cs.counters, cs.step_flag, cs.ranges,
-                                         cs.tfill, cs.tbig, cs.torder, cs.tck, cs.units, cs.ck_cap);
+                                         cs.tfill, cs.tbig);
   TGS_LAUNCHED();
+  // the raster tile order reads only the ranges: it runs beside the emission
+  // and the sorts (one CTA on a high-priority stream), joined before the
+  // forward raster
+  TGS_CUDA(cudaEventRecord(cs.ev_fork, s));
+  TGS_CUDA(cudaStreamWaitEvent(cs.aux, cs.ev_fork, 0));
+  k_tile_order<<<1, TS_THREADS, 0, cs.aux>>>(cs.ranges, (uint32_t)tiles, cs.counters, cs.torder, cs.tck, cs.units,
+                                             cs.ck_cap);
+  TGS_LAUNCHED();
+  TGS_CUDA(cudaEventRecord(cs.ev_join, cs.aux));
   const unsigned g_e = std::min<uint64_t>(div_up(V, EM_THREADS), 8 * NSM);
   // the big and middle Gaussian lists live in the two halves of dkeys (2 V words)
   k_emit_tiles<<<g_e, EM_THREADS, 0, s>>>(V, cs.ntiles, cs.rect, cs.depth, TX, cs.ranges, cs.tfill, cs.pkeys,
@@ -617,6 +664,7 @@ void bin_tiles(uint64_t V, int TX, int TY, CamState& cs, cudaStream_t s) {
   k_tile_sort_big<<<NSM, SORT_BIG_THREADS, 2 * SORT_BIG * sizeof(unsigned long long), s>>>(
       cs.ranges, cs.tbig, cs.counters, cs.pkeys, cs.pvals, cs.cap_pairs);
   TGS_LAUNCHED();
+  TGS_CUDA(cudaStreamWaitEvent(s, cs.ev_join, 0));
 }
 
 }  // namespace tgs
