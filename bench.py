@@ -536,6 +536,8 @@ def run_street(args, rank, world, local):
         # drive prefetches the next frame only, at a stricter threshold
         forms_fast, _, t_train_f = drive_forms(torch, tgs, table, tb, host, fast, targets_f, vis_f, spheres, world,
                                                local, dev, threshold=0.5, horizon_mask=0b01)
+    train_ids = [i for i in range(nc) if i % 10 != 0]
+    ablation_fast = ablation_eval(args, tgs, host, base, fast, targets_f, train_ids) if args.ablation else None
     del targets_f
     table.close()
     del table
@@ -641,10 +643,11 @@ def run_street(args, rank, world, local):
     out["stage_steps"] = STAGE_STEPS
     out["drive_b"] = drive_b
     out["ablation"] = ablation
+    out["ablation_fast"] = ablation_fast
     return out
 
 
-def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=40, warm=5):
+def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=120, warm=5):
     """Tab. 5 analogue on the street scene (BF16 record, exact next-batch
     prefetch as the full method): the same n steps with differential streaming
     off (every selection evicts the cache and streams the selected set again),
@@ -686,11 +689,12 @@ def ablation_eval(args, tgs, host, base, cams, targets, train_ids, n=40, warm=5)
             torch.cuda.synchronize()
             st = t.stats()
             ms = e0.elapsed_time(e1) / n
+            d = {kk: st[kk] - s0[kk] for kk in STAT_KEYS}
             res[name] = {"ms_per_step": round(ms, 3), "iters_per_s": round(1e3 / ms, 2),
                          "h2d_gb_per_step": round((st["bytes_h2d"] - s0["bytes_h2d"]) / n / 1e9, 4),
                          "d2h_gb_per_step": round((st["bytes_d2h"] - s0["bytes_d2h"]) / n / 1e9, 4),
                          "stall_ms_per_step": round((st["stall_ms"] - s0["stall_ms"]) / n, 3),
-                         "render_blocks": st["last_render_blocks"]}
+                         "render_blocks": st["last_render_blocks"], "churn": churn(d)}
         except Exception as e:  # a variant that does not fit the configuration
             res[name] = {"error": str(e)[:200]}
         t.close()
@@ -1176,6 +1180,7 @@ def main():
         line["drive_b"] = res["drive_b"]
         if res.get("ablation"):
             line["ablation"] = res["ablation"]
+            line["ablation_link_bound_drive"] = res["ablation_fast"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not city:
         line["cpu_baseline"] = cpu_baseline_street(res) if street else cpu_baseline(res)
     res["table"].close()

@@ -1,4 +1,7 @@
 """Comparison helpers shared by the GPU parity tests (test infrastructure)."""
+import json
+import os
+
 import numpy as np
 
 import scenes
@@ -29,3 +32,17 @@ def c1_inputs(orc, block_size=1250, n=20000, size=256):
     perm, Pm = orc.create(cfg["params"], block_size)
     target_p = scenes.perturb(cfg["params"], seed=77)
     return cfg, perm, Pm, target_p
+
+
+def report(config, form, **errors):
+    """Appends one record of measured errors against the FP64 oracle (image
+    max-abs on slack-free pixels, gradient rel-L2, ...) to the JSON-lines
+    file named by TGS_PARITY_REPORT, when set; the tests assert their bounds
+    either way."""
+    path = os.environ.get("TGS_PARITY_REPORT")
+    if not path:
+        return
+    rec = {"config": config, "form": form}
+    rec.update({k: float(v) for k, v in errors.items()})
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity_util import image_within, rel_l2
+from parity_util import image_within, rel_l2, report
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +56,8 @@ def test_aerial_2m_1080p_autograd_and_finite_differences(orc, tgs):
     for a, b in GROUPS:
         assert rel_l2(g[vis, a:b], go[vis, a:b]) < 1e-3, (a, b)
     assert not g[~vis].any()
+    report("c2 aerial-2M 1920x1080 (autograd)", "fp32", image_maxabs=err, slack_frac=frac,
+           grad59_rel_l2=rel_l2(g[vis], go[vis]))
 
     # ---- finite differences on a seeded 2,000-Gaussian visible subset
     rng = np.random.default_rng(22)

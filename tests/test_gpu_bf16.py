@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity_util import c1_inputs, image_within, rel_l2
+from parity_util import c1_inputs, image_within, rel_l2, report
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,13 @@ def test_bf16_step_matches_oracle(orc, tgs, B):
     vo = o["records"][0]["S"][:, orc.VISIBLE] != 0
     for q in range(9):
         assert rel_l2(rec["grad2d"][vg & vo, q], o["g2"][0][vg & vo, q]) < 1e-3, q
+    # the same image and 2D gradients against the oracle on the unrounded
+    # FP32 table: the error the BF16 record itself adds
+    o32 = orc.render(Pm.astype(np.float64)[o["ids"]], cams[0], with_slack=True)
+    err32 = float(np.abs(rec["image"].astype(np.float64) - o32["img"]).max())
+    report(f"c1 cube-20k 256x256 B={B}", "bf16", image_maxabs=err, slack_frac=frac,
+           grad2d_rel_l2=max(rel_l2(rec["grad2d"][vg & vo, q], o["g2"][0][vg & vo, q]) for q in range(9)),
+           image_maxabs_vs_fp32_table=err32)
     p_g, m1, m2, st = table.state()
     ids, touched = o["ids"], o["touched"].astype(bool)
     # first moments: m = 0.1 g, stored as BF16 (one of the two neighbours)

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity_util import image_within, rel_l2
+from parity_util import image_within, rel_l2, report
 from test_gpu_bf16 import bf16_round, bf16_ulp
 
 pytestmark = pytest.mark.gpu
@@ -85,8 +85,11 @@ def test_city_batch4_bf16_step_matches_oracle(orc, tgs):
         touched |= vo
         both = vg & vo
         assert both.sum() > 1000, j
+        r2 = [rel_l2(rec["grad2d"][both, q], g2[both, q]) for q in range(9)]
         for q in range(9):
-            assert rel_l2(rec["grad2d"][both, q], g2[both, q]) < 1e-3, (j, q)
+            assert r2[q] < 1e-3, (j, q)
+        report(f"c4 city-2M batch 4 1920x1080 camera {j}", "bf16", image_maxabs=err, slack_frac=frac,
+               grad2d_rel_l2=max(r2))
     # step counters: blocks with a touched row
     want_steps = np.zeros(K, np.uint32)
     want_steps[np.unique(ids[touched] // B)] = 1

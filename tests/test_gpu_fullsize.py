@@ -13,14 +13,17 @@ Gaussians outside that ball are culled by Level 2 in both, so
     the GPU's image on both sides);
   - the touched rows moved by one Adam step of that gradient, the others
     not at all, and the refreshed spheres of the rendered blocks are those of
-    their updated rows."""
+    their updated rows;
+  - a render of the same camera from the BF16 record matches the oracle on
+    the same rows with their SH rest rounded to BF16."""
 import math
 
 import numpy as np
 import pytest
 
 import scenes
-from parity_util import image_within, rel_l2
+from parity_util import image_within, rel_l2, report
+from test_gpu_bf16 import bf16_round
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +59,13 @@ def test_street_100m_step_matches_oracle(orc, tgs):
     p_after, m1_after, _ = table.state_rows(all_ids)
     sph_after = table.spheres()[blocks]
     table.close()
+    # the BF16 record (SH rest and moments BF16 in the host tier and the
+    # cache): a render of the same camera
+    tb = tgs.TideTable(host, block_size=4096, max_batch=1, max_width=W, max_height=H, cache_blocks=cache,
+                       spare_slots=512, prefetch_mode=0, loss=2, host_bf16=1, stochastic_round=1)
+    tb.render(cam, img)
+    gpu_img_bf16 = img.cpu().numpy()
+    tb.close()
     del host
 
     # the oracle on the neighbourhood, in the table's (Morton) row order
@@ -75,6 +85,16 @@ def test_street_100m_step_matches_oracle(orc, tgs):
     assert err <= 1e-4 and frac < 0.05
     err, frac = image_within(rec["image"], o)
     assert err <= 1e-4 and frac < 0.05
+    img_err, img_frac = err, frac
+    # BF16 form against the oracle on the same rows with their SH rest rounded
+    Pbf = P.copy()
+    Pbf[:, 14:] = bf16_round(P[:, 14:])
+    ob = orc.render(Pbf, ca, with_slack=True)
+    err_b, frac_b = image_within(gpu_img_bf16, ob)
+    assert err_b <= 1e-4 and frac_b < 0.05
+    report("c3 street-100M 1600x900 render", "bf16", image_maxabs=err_b, slack_frac=frac_b,
+           image_maxabs_vs_fp32_table=float(np.abs(gpu_img_bf16.astype(np.float64) - o["img"]).max()))
+    del ob, Pbf
     lo, _ = orc.loss(o["img"][None], tgt.astype(np.float64), 2)
     assert abs(lval - lo) <= 1e-4 * lo
 
@@ -96,13 +116,16 @@ def test_street_100m_step_matches_oracle(orc, tgs):
     sg = np.sign(rec["image"][None].astype(np.float64) - tg)
     dimg = 0.8 * sg / nval - 0.2 * ossim.ssim_grad(o["img"][None], tg)
     g_ref, g2_ref = orc.render_grad(P, ca, o, dimg[0])
+    r2 = [rel_l2(rec["grad2d"][at[both], q], g2_ref[both, q]) for q in range(9)]
     for q in range(9):
-        assert rel_l2(rec["grad2d"][at[both], q], g2_ref[both, q]) < 1e-3, q
+        assert r2[q] < 1e-3, q
     # 59-parameter gradients of the touched rows from the first moment
     sel = np.searchsorted(all_ids, oid[both])  # all_ids ascends
     assert np.array_equal(all_ids[sel], oid[both])
     g_gpu = m1_after[sel].astype(np.float64) / 0.1
     assert rel_l2(g_gpu, g_ref[both]) < 1e-3
+    report("c3 street-100M 1600x900 step", "fp32", image_maxabs=img_err, slack_frac=img_frac, grad2d_rel_l2=max(r2),
+           grad59_rel_l2=rel_l2(g_gpu, g_ref[both]))
     for f in range(59):
         assert rel_l2(g_gpu[:, f], g_ref[both, f]) < 1e-3, f
     # one Adam step of the reference gradient (zero moments, step 1)

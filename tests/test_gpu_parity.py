@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity_util import c1_inputs, image_within, rel_l2
+from parity_util import c1_inputs, image_within, rel_l2, report
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +82,7 @@ def _check_step(orc, tgs, params, B, camd, target, loss, W, H, **cfg):
         assert np.array_equal(sg, so), t
     err, frac = image_within(rec["image"], orec)
     assert err <= 1e-4 and frac < 0.05
+    img_err = err
     clean = orec["slack"] == 0
     np.testing.assert_allclose(rec["t_final"][clean], orec["T"][clean], atol=1e-5)
     assert np.array_equal(rec["n_last"][clean], orec["nlast"][clean])
@@ -113,6 +114,9 @@ def _check_step(orc, tgs, params, B, camd, target, loss, W, H, **cfg):
     assert rel_l2(g_gpu[touched], g_ref[touched]) < 1e-3
     for f in range(59):
         assert rel_l2(g_gpu[touched, f], g_ref[touched, f]) < 1e-3, f
+    report(f"c1 cube {params.shape[0]} {W}x{H} loss {loss}", "fp32", image_maxabs=img_err, slack_frac=frac,
+           grad2d_rel_l2=max(rel_l2(rec["grad2d"][vo & vg, q], g2_ref[vo & vg, q]) for q in range(9)),
+           grad59_rel_l2=rel_l2(g_gpu[touched], g_ref[touched]))
     # ---- masked Adam: untouched rows bit-identical, touched rows moved by one
     # Adam step of the reference gradient (from zero moments, step 1)
     moved = np.zeros(len(p_g), bool)
