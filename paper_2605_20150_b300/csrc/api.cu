@@ -487,6 +487,10 @@ tgs_status tgs_get_stats(tgs_table* t, tgs_stats* out) {
     *out = t->t.stats;
     unsigned long long churn[2];
     TGS_CUDA(cudaStreamSynchronize(t->t.comp));
+    if (t->t.predictor) {
+      TGS_CUDA(cudaStreamSynchronize(t->t.ctl));
+      mlp_check(*t->t.predictor);
+    }
     TGS_CUDA(cudaMemcpy(churn, t->t.churn_dev, sizeof(churn), cudaMemcpyDeviceToHost));
     out->block_updates = churn[0];
     out->cold_updates = churn[1];

@@ -101,9 +101,5 @@ __device__ __forceinline__ KeyPath key_path(const DevCam& c, float mx, float my,
   return k;
 }
 
-__device__ __forceinline__ float splat_alpha(float opac, float power, float& G) {
-  G = __expf(power);
-  return fminf(ALPHA_MAX, __fmul_rn(opac, G));
-}
 
 }  // namespace tgs

@@ -1,13 +1,16 @@
 // Learned block-prefetch predictor on the GPU.
 //
-// Inference (every step of the learned-prefetch mode) is one fused kernel per
-// 64 block rows: layer 1 (the pose part is a shared 96 x 256 product computed
-// once per step; the per-block part has 6 inputs) in FP32 into a BF16 tile in
-// shared memory, layer 2 (256 x 256) on the tensor cores with BF16 mma.sync
-// and FP32 accumulation, and layer 3 (256 x 4) plus bias folded into the
-// epilogue with quad shuffles.  Training kernels (offline, on logged
-// visibility) are FP32 SIMT: BCE gradient, the two 256-wide products of the
-// backward, column sums, and AdamW on FP32 master weights.
+// Inference (every step of the learned-prefetch mode) is one fused kernel on
+// the tcgen05 tensor cores, persistent over 128-row tiles of block rows:
+// layer 1 (the pose part is a shared 96 x 256 product computed once per step;
+// the per-block part has 6 inputs) in FP32 into a BF16 operand tile in shared
+// memory, layer 2 (256 x 256, BF16 operands, FP32 accumulator in tensor
+// memory) as 16 tcgen05.mma of M = 128, N = 256, K = 16 issued by one thread,
+// and layer 3 (256 x 4) plus biases in the epilogue, one accumulator row
+// (tcgen05.ld) per thread.  Training kernels (offline, on logged visibility)
+// are FP32 SIMT: BCE gradient, the two 256-wide products of the backward,
+// column sums, and AdamW on FP32 master weights.
+#include <algorithm>
 #include <cmath>
 #include <random>
 #include <vector>
@@ -18,7 +21,6 @@
 namespace tgs {
 namespace {
 
-constexpr int W2S = MLP_H + 8;  // padded shared-memory row (bf16 elements)
 
 __global__ void k_mlp_feat(const float4* __restrict__ sph, uint64_t K, uint64_t M, DevCam c, float zf,
                            float* __restrict__ feat) {
@@ -61,114 +63,220 @@ __global__ void k_mlp_pose(const float* __restrict__ P, PoseVec pose, float* __r
   if (j < MLP_NPOSE) pose_out[j] = pose.v[j];
 }
 
-__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+// ---- the forward on the 5th-generation tensor cores (tcgen05, sm_100+):
+// persistent CTAs of 128 threads, one 128-row tile at a time.  W2^T (BF16,
+// 256 x 256) is staged once per CTA in shared memory in the canonical K-major
+// layout without swizzle: 8-row x 16-byte core matrices, element (r, k) of an
+// R-row operand at (k / 8) * 16 R + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+// bytes, so a descriptor's leading-dimension offset (next core matrix along
+// K) is 16 R bytes and its stride-dimension offset (next 8 rows) 128 bytes.
+// Per tile: layer 1 (FP32, thread t = row t) writes h1 as BF16 in the same
+// layout, one thread issues the 16 MMAs (M = 128, N = 256, K = 16 each) into
+// a 128 x 256 FP32 accumulator in tensor memory and commits them to an
+// mbarrier; after the wait each warp reads its 32 accumulator lanes (rows)
+// with tcgen05.ld, and each thread applies bias, ReLU and layer 3 to its row.
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_COLS = MLP_H;                         // accumulator columns (FP32)
+constexpr uint32_t TC_B_BYTES = (uint32_t)MLP_H * MLP_H * 2;  // 128 KB
+constexpr uint32_t TC_A_BYTES = (uint32_t)TC_M * MLP_H * 2;   // 64 KB
+constexpr uint32_t TC_F_FLOATS = MLP_NFEAT * MLP_H + MLP_H + MLP_H + MLP_H * MLP_OUT + 4 + TC_M * 8;
+constexpr uint32_t TC_SPIN_MAX = 1u << 22;  // try_wait polls before a wait gives up
+// instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MLP_H >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cm_off(uint32_t r, uint32_t k, uint32_t R) {
+  return (k >> 3) * (R * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// 64 rows per CTA, 4 warps of 16 rows; shared: W2^T bf16 [256][264], h1 bf16
-// [64][264], W1 block part [6][256], pose term, b2, W3 [256][4], b3, features.
-__global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ P, const __nv_bfloat16* __restrict__ w2t,
-                                                const float* __restrict__ pterm, const float* __restrict__ feat,
-                                                uint64_t M, float* __restrict__ z3, __nv_bfloat16* __restrict__ h1g,
-                                                float* __restrict__ h2g, const uint32_t* __restrict__ rows_dev) {
-  // rows_dev (device, may be null): only the first *rows_dev rows are wanted
-  if (rows_dev && (uint64_t)blockIdx.x * MLP_ROWS_PER_CTA >= *rows_dev) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* w2s = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* h1s = w2s + MLP_H * W2S;
-  float* w1b = reinterpret_cast<float*>(h1s + MLP_ROWS_PER_CTA * W2S);
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (all >> 4), descriptor version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < TC_SPIN_MAX; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// rows_dev (device, may be null): only the first *rows_dev of the M rows are
+// wanted.  err (device): set when a wait for the tensor cores runs out.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(const float* __restrict__ P,
+                                                             const __nv_bfloat16* __restrict__ w2t,
+                                                             const float* __restrict__ pterm,
+                                                             const float* __restrict__ feat, uint64_t M,
+                                                             const uint32_t* __restrict__ rows_dev,
+                                                             float* __restrict__ z3, __nv_bfloat16* __restrict__ h1g,
+                                                             float* __restrict__ h2g, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* sB = tsm;
+  unsigned char* sA = tsm + TC_B_BYTES;
+  float* w1b = reinterpret_cast<float*>(sA + TC_A_BYTES);  // [6][256]
   float* pt = w1b + MLP_NFEAT * MLP_H;
   float* b2 = pt + MLP_H;
-  float* w3 = b2 + MLP_H;
+  float* w3 = b2 + MLP_H;  // [256][4]
   float* b3 = w3 + MLP_H * MLP_OUT;
-  float* fs = b3 + 4;
-  const int tid = threadIdx.x;
-  const uint64_t row0 = (uint64_t)blockIdx.x * MLP_ROWS_PER_CTA;
-  // stage weights
-  for (int e = tid; e < MLP_H * MLP_H / 8; e += 128) {
-    int n = e / (MLP_H / 8), k8 = e % (MLP_H / 8);
-    *reinterpret_cast<uint4*>(w2s + n * W2S + 8 * k8) = *reinterpret_cast<const uint4*>(w2t + (uint64_t)n * MLP_H + 8 * k8);
+  float* fs = b3 + 4;  // [128][8]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(fs + TC_M * 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t rows = M;
+  if (rows_dev && (uint64_t)*rows_dev < rows) rows = *rows_dev;
+  const uint32_t ntiles = (uint32_t)((rows + TC_M - 1) / TC_M);
+  if (blockIdx.x >= ntiles) return;  // uniform, before any tensor-memory allocation
+  for (uint32_t e = tid; e < MLP_H * (MLP_H / 8); e += TC_THREADS) {
+    const uint32_t n = e / (MLP_H / 8), k8 = e % (MLP_H / 8);
+    *reinterpret_cast<uint4*>(sB + cm_off(n, 8 * k8, MLP_H)) =
+        *reinterpret_cast<const uint4*>(w2t + (uint64_t)n * MLP_H + 8 * k8);
   }
-  for (int e = tid; e < MLP_NFEAT * MLP_H; e += 128) w1b[e] = P[MLP_OFF_W1 + (uint64_t)MLP_NPOSE * MLP_H + e];
-  for (int e = tid; e < MLP_H; e += 128) {
+  for (uint32_t e = tid; e < MLP_NFEAT * MLP_H; e += TC_THREADS) w1b[e] = P[MLP_OFF_W1 + (uint64_t)MLP_NPOSE * MLP_H + e];
+  for (uint32_t e = tid; e < MLP_H; e += TC_THREADS) {
     pt[e] = pterm[e];
     b2[e] = P[MLP_OFF_B2 + e];
   }
-  for (int e = tid; e < MLP_H * MLP_OUT; e += 128) w3[e] = P[MLP_OFF_W3 + e];
+  for (uint32_t e = tid; e < MLP_H * MLP_OUT; e += TC_THREADS) w3[e] = P[MLP_OFF_W3 + e];
   if (tid < 4) b3[tid] = P[MLP_OFF_B3 + tid];
-  for (int e = tid; e < MLP_ROWS_PER_CTA * 8; e += 128) fs[e] = feat[row0 * 8 + e];
-  __syncthreads();
-  // layer 1
-  for (int e = tid; e < MLP_ROWS_PER_CTA * MLP_H; e += 128) {
-    const int r = e / MLP_H, j = e % MLP_H;
-    float z = pt[j];
-#pragma unroll
-    for (int i = 0; i < MLP_NFEAT; ++i) z += fs[r * 8 + i] * w1b[i * MLP_H + j];
-    __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(z, 0.f));
-    h1s[r * W2S + j] = h;
-    if (h1g) h1g[(row0 + r) * MLP_H + j] = h;
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(tmem_slot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  // layer 2 on the tensor cores
-  const int w = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
-  float acc[MLP_H / 8][4];
-#pragma unroll
-  for (int nt = 0; nt < MLP_H / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-  const __nv_bfloat16* ar0 = h1s + (16 * w + g) * W2S;
-  const __nv_bfloat16* ar8 = ar0 + 8 * W2S;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(sA), b0 = (uint32_t)__cvta_generic_to_shared(sB);
+  uint32_t parity = 0;
+  bool ok = true;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t r0 = (uint64_t)t * TC_M;
+    for (uint32_t e = tid; e < TC_M * 8; e += TC_THREADS) {
+      const uint64_t r = r0 + e / 8;
+      fs[e] = r < M ? feat[r * 8 + e % 8] : 0.f;
+    }
+    __syncthreads();
+    // layer 1: thread tid computes row r0 + tid
+    const uint64_t row = r0 + (uint64_t)tid;
 #pragma unroll 1
-  for (int k0 = 0; k0 < MLP_H; k0 += 16) {
-    const uint32_t a0 = *reinterpret_cast<const uint32_t*>(ar0 + k0 + 2 * q);
-    const uint32_t a1 = *reinterpret_cast<const uint32_t*>(ar8 + k0 + 2 * q);
-    const uint32_t a2 = *reinterpret_cast<const uint32_t*>(ar0 + k0 + 8 + 2 * q);
-    const uint32_t a3 = *reinterpret_cast<const uint32_t*>(ar8 + k0 + 8 + 2 * q);
+    for (int k0 = 0; k0 < MLP_H; k0 += 8) {
+      uint32_t pk[4];
 #pragma unroll
-    for (int nt = 0; nt < MLP_H / 8; ++nt) {
-      const __nv_bfloat16* br = w2s + (8 * nt + g) * W2S + k0;
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(br + 2 * q);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(br + 8 + 2 * q);
-      mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+      for (int q = 0; q < 4; ++q) {
+        float z[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = k0 + 2 * q + u;
+          float a = pt[j];
+#pragma unroll
+          for (int i = 0; i < MLP_NFEAT; ++i) a += fs[tid * 8 + i] * w1b[i * MLP_H + j];
+          z[u] = fmaxf(a, 0.f);
+        }
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[0], z[1]);
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(sA + cm_off((uint32_t)tid, (uint32_t)k0, TC_M)) = v;
+      if (h1g && row < M) *reinterpret_cast<uint4*>(h1g + row * MLP_H + k0) = v;
     }
+    // the tile's h1 (generic-proxy stores) becomes visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+      for (uint32_t s2 = 0; s2 < MLP_H / 16; ++s2) {
+        const uint64_t ad = smem_desc(a0 + 2 * s2 * (TC_M * 16), TC_M * 16, 128);
+        const uint64_t bd = smem_desc(b0 + 2 * s2 * (MLP_H * 16), MLP_H * 16, 128);
+        tc_mma(tmem, ad, bd, s2 > 0 ? 1u : 0u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                   : "memory");
+    }
+    if (!mbar_wait(mb, parity)) {
+      ok = false;
+      if (tid == 0) atomicOr(err, 1u);
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+      // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31 (row tid)
+      float lz[MLP_OUT];
+#pragma unroll
+      for (int o = 0; o < MLP_OUT; ++o) lz[o] = b3[o];
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < TC_COLS; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float h = fmaxf(v[j] + b2[c0 + j], 0.f);
+          v[j] = h;
+#pragma unroll
+          for (int o = 0; o < MLP_OUT; ++o) lz[o] += h * w3[(c0 + j) * MLP_OUT + o];
+        }
+        if (h2g && row < M) {
+          float4* d = reinterpret_cast<float4*>(h2g + row * MLP_H + c0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+      if (row < M) {
+#pragma unroll
+        for (int o = 0; o < MLP_OUT; ++o) z3[row * MLP_OUT + o] = lz[o];
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();  // accumulator, features and the A tile are rewritten next
+    if (!__syncthreads_or(!ok)) continue;
+    break;
   }
-  // epilogue: bias + ReLU, layer 3 folded in
-  float lz[2][MLP_OUT] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  const uint64_t ra = row0 + 16 * w + g, rb = ra + 8;
-#pragma unroll
-  for (int nt = 0; nt < MLP_H / 8; ++nt) {
-    const int col = 8 * nt + 2 * q;
-    const float h00 = fmaxf(acc[nt][0] + b2[col], 0.f), h01 = fmaxf(acc[nt][1] + b2[col + 1], 0.f);
-    const float h10 = fmaxf(acc[nt][2] + b2[col], 0.f), h11 = fmaxf(acc[nt][3] + b2[col + 1], 0.f);
-    if (h2g) {
-      *reinterpret_cast<float2*>(h2g + ra * MLP_H + col) = make_float2(h00, h01);
-      *reinterpret_cast<float2*>(h2g + rb * MLP_H + col) = make_float2(h10, h11);
-    }
-#pragma unroll
-    for (int h = 0; h < MLP_OUT; ++h) {
-      lz[0][h] += h00 * w3[col * MLP_OUT + h] + h01 * w3[(col + 1) * MLP_OUT + h];
-      lz[1][h] += h10 * w3[col * MLP_OUT + h] + h11 * w3[(col + 1) * MLP_OUT + h];
-    }
-  }
-#pragma unroll
-  for (int h = 0; h < MLP_OUT; ++h) {
-#pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {
-      lz[0][h] += __shfl_xor_sync(0xffffffffu, lz[0][h], o);
-      lz[1][h] += __shfl_xor_sync(0xffffffffu, lz[1][h], o);
-    }
-  }
-  if (q == 0) {
-#pragma unroll
-    for (int h = 0; h < MLP_OUT; ++h) {
-      z3[ra * MLP_OUT + h] = lz[0][h] + b3[h];
-      z3[rb * MLP_OUT + h] = lz[1][h] + b3[h];
-    }
-  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
+
+constexpr size_t TC_SMEM = TC_B_BYTES + TC_A_BYTES + TC_F_FLOATS * sizeof(float) + 16;
 
 __device__ __forceinline__ float softplus(float x) { return x > 20.f ? x : log1pf(__expf(x)); }
 
@@ -389,12 +497,17 @@ __global__ void k_mlp_threshold_cand(const float* __restrict__ z3, const uint32_
   if (vis) atomicOr(bits + (cid[r] >> 5), 1u << (cid[r] & 31));
 }
 
-size_t fwd_smem_bytes() {
-  return (size_t)MLP_H * W2S * 2 + (size_t)MLP_ROWS_PER_CTA * W2S * 2 +
-         sizeof(float) * (MLP_NFEAT * MLP_H + MLP_H + MLP_H + MLP_H * MLP_OUT + 4 + MLP_ROWS_PER_CTA * 8);
-}
+
+// persistent CTAs: one per SM at most (each holds 208 KB of shared memory)
+unsigned tc_grid(uint64_t M) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((M + TC_M - 1) / TC_M, NSM)); }
 
 }  // namespace
+
+void mlp_check(Mlp& m) {
+  uint32_t e = 0;
+  TGS_CUDA(cudaMemcpy(&e, m.err, sizeof(e), cudaMemcpyDeviceToHost));
+  TGS_CHECK(e == 0, TGS_ERR_TIMEOUT, "predictor: a wait for the tensor cores ran out");
+}
 
 void mlp_alloc(Mlp& m, uint64_t max_rows, uint32_t seed) {
   m.max_rows = (max_rows + MLP_ROWS_PER_CTA - 1) / MLP_ROWS_PER_CTA * MLP_ROWS_PER_CTA;
@@ -436,14 +549,16 @@ void mlp_alloc(Mlp& m, uint64_t max_rows, uint32_t seed) {
   TGS_CUDA(cudaMemcpy(m.params, h.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
   TGS_CUDA(cudaMemset(m.m, 0, MLP_NPARAM * sizeof(float)));
   TGS_CUDA(cudaMemset(m.v, 0, MLP_NPARAM * sizeof(float)));
-  TGS_CUDA(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes()));
+  TGS_CUDA(cudaMalloc(&m.err, sizeof(uint32_t)));
+  TGS_CUDA(cudaMemset(m.err, 0, sizeof(uint32_t)));
+  TGS_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
   mlp_refresh_bf16(m, 0);
   TGS_CUDA(cudaDeviceSynchronize());
 }
 
 void mlp_free(Mlp& m) {
   void* p[] = {m.params, m.grads, m.m, m.v, m.w2t, m.w2r, m.pose, m.pterm, m.feat, m.h1, m.h2, m.z3, m.dh2, m.dh1,
-               m.dz3, m.loss, m.cflag, m.cpos, m.cid, m.ccount, m.cscratch};
+               m.dz3, m.loss, m.cflag, m.cpos, m.cid, m.ccount, m.cscratch, m.err};
   for (void* x : p)
     if (x) cudaFree(x);
   if (m.loss_host) cudaFreeHost(m.loss_host);
@@ -492,8 +607,8 @@ void mlp_forward(Mlp& m, const float4* spheres, uint64_t K, const tgs_camera* hi
   TGS_LAUNCHED();
   k_mlp_pose<<<1, MLP_H, 0, s>>>(m.params, pv, m.pose, m.pterm);
   TGS_LAUNCHED();
-  k_mlp_fwd<<<(unsigned)(M / MLP_ROWS_PER_CTA), 128, fwd_smem_bytes(), s>>>(
-      m.params, m.w2t, m.pterm, m.feat, M, m.z3, keep ? m.h1 : nullptr, keep ? m.h2 : nullptr, nullptr);
+  k_mlp_fwd_tc<<<tc_grid(M), TC_THREADS, TC_SMEM, s>>>(m.params, m.w2t, m.pterm, m.feat, M, nullptr, m.z3,
+                                                       keep ? m.h1 : nullptr, keep ? m.h2 : nullptr, m.err);
   TGS_LAUNCHED();
   if (logits && logits != m.z3)
     TGS_CUDA(cudaMemcpyAsync(logits, m.z3, K * MLP_OUT * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -540,6 +655,7 @@ float mlp_train_step(Mlp& m, uint64_t K, const float* labels, float pw, float lr
   }
   TGS_CUDA(cudaMemcpyAsync(m.loss_host, m.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
   TGS_CUDA(cudaStreamSynchronize(s));
+  mlp_check(m);
   return *m.loss_host;
 }
 
@@ -561,8 +677,8 @@ void mlp_predict_near(Mlp& m, const float4* spheres, uint64_t K, const tgs_camer
   TGS_LAUNCHED();
   k_mlp_pose<<<1, MLP_H, 0, s>>>(m.params, pv, m.pose, m.pterm);
   TGS_LAUNCHED();
-  k_mlp_fwd<<<(unsigned)(M / MLP_ROWS_PER_CTA), 128, fwd_smem_bytes(), s>>>(m.params, m.w2t, m.pterm, m.feat, M, m.z3,
-                                                                            nullptr, nullptr, m.ccount);
+  k_mlp_fwd_tc<<<tc_grid(M), TC_THREADS, TC_SMEM, s>>>(m.params, m.w2t, m.pterm, m.feat, M, m.ccount, m.z3, nullptr,
+                                                       nullptr, m.err);
   TGS_LAUNCHED();
   const float zthr = std::log(thr / (1.f - thr));
   TGS_CUDA(cudaMemsetAsync(bits, 0, (K + 31) / 32 * sizeof(uint32_t), s));

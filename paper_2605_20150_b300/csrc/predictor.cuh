@@ -1,6 +1,8 @@
 // Learned block-prefetch predictor (not in the paper): a 3-layer MLP that
 // maps the last 8 camera poses plus per-block centroid/extent features to the
-// block's visibility in the next 4 iterations.
+// block's visibility in the next 4 iterations.  The forward's 256 x 256 layer
+// runs on the tcgen05 tensor cores (BF16 operands in shared memory, FP32
+// accumulator in tensor memory).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -48,11 +50,15 @@ struct Mlp {
   uint32_t* cid = nullptr;       //   block of each row,
   uint32_t* ccount = nullptr;    //   device count
   void* cscratch = nullptr;
+  uint32_t* err = nullptr;       // device word: a tensor-core wait ran out
   uint32_t step = 0;
 };
 
 void mlp_alloc(Mlp& m, uint64_t max_rows, uint32_t seed);
 void mlp_free(Mlp& m);
+// Throws TGS_ERR_TIMEOUT if a forward's wait for the tensor cores ran out
+// (reads a device word: synchronous).
+void mlp_check(Mlp& m);
 void mlp_refresh_bf16(Mlp& m, cudaStream_t s);
 // pose vector (96) of a camera history (8 cameras, oldest first, last = current)
 void mlp_pose_host(const tgs_camera* hist, float out[MLP_NPOSE]);

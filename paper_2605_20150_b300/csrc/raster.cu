@@ -486,10 +486,12 @@ __device__ __forceinline__ bool splat_hits(const WarpPix& q, float x, float y, f
 }
 
 // One splat as staged in shared memory, with the conic folded into the
-// power's coefficients: power = dx (a2 dx + b2 dy) + c2 dy^2 with a2 = -A/2,
-// b2 = -B, c2 = -C/2 (exact scalings), evaluated as
-//   power = fma(dx, fma(b2, dy, a2 dx), c2 (dy dy))
-// by the forward and the backward alike, so both take the same alphas.
+// power's coefficients in base 2: power2 = power log2(e) = dx (a2 dx + b2 dy)
+// + c2 dy^2 with a2 = -A log2(e)/2, b2 = -B log2(e), c2 = -C log2(e)/2,
+// evaluated as
+//   power2 = fma(dx, fma(b2, dy, a2 dx), c2 (dy dy)),  G = 2^power2
+// by the forward and the backward alike, so both take the same alphas (the
+// power's sign tests are unchanged by the positive scale).
 struct Splat {
   float4 a;  // x, y, a2, b2
   float4 b;  // c2, opacity, r, g
@@ -497,6 +499,18 @@ struct Splat {
   uint32_t id;
 };
 
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LN2 = 0.6931471805599453f;
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// alpha = min(0.99, o G), G = 2^power2 (the base-2 power of the staged splat)
+__device__ __forceinline__ float splat_alpha2(float opac, float power2, float& G) {
+  G = ex2_approx(power2);
+  return fminf(ALPHA_MAX, __fmul_rn(opac, G));
+}
 __device__ __forceinline__ float splat_power(float a2dx, float b2, float c2, float dx, float dy, float dyy) {
   return __fmaf_rn(dx, __fmaf_rn(b2, dy, a2dx), __fmul_rn(c2, dyy));
 }
@@ -508,8 +522,8 @@ __device__ __forceinline__ bool stage_splat(const uint32_t* __restrict__ pvals, 
   const float2 g = xy[id];
   const float4 co = conic_o[id];
   const float4 cc = rgb[id];
-  slot->a = make_float4(g.x, g.y, -0.5f * co.x, -co.y);
-  slot->b = make_float4(-0.5f * co.z, co.w, cc.x, cc.y);
+  slot->a = make_float4(g.x, g.y, -0.5f * LOG2E * co.x, -LOG2E * co.y);
+  slot->b = make_float4(-0.5f * LOG2E * co.z, co.w, cc.x, cc.y);
   slot->c = cc.z;
   slot->id = id;
   return splat_hits(q, g.x, g.y, co.x, co.y, co.z, co.w);
@@ -577,7 +591,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) k_raster_fwd(const uint2* __re
         const float dy = __fsub_rn((float)(q.py0 + k), a.y);
         const float power = splat_power(a2dx, a.w, bb.x, dx, dy, __fmul_rn(dy, dy));
         float G;
-        const float alpha = splat_alpha(bb.y, power, G);
+        const float alpha = splat_alpha2(bb.y, power, G);
         const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
         const bool ok = live[k] && power <= 0.f && alpha >= ALPHA_MIN;
         const bool stop = ok && Tn < T_STOP;
@@ -786,7 +800,7 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         const float dxy = __fmul_rn(dx, dy);
         const float power = splat_power(a2dx, a.w, bb.x, dx, dy, dyy);
         float G;
-        const float alpha = splat_alpha(bb.y, power, G);
+        const float alpha = splat_alpha2(bb.y, power, G);
         const bool ok = pos < last[k] && power <= 0.f && alpha >= ALPHA_MIN;
         contrib |= ok;
         const float al = ok ? alpha : 0.f;
@@ -813,8 +827,9 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       if (__ballot_sync(0xffffffffu, contrib)) {
 #pragma unroll
         for (int f = 0; f < 9; ++f) red[9 * nslot + f][lane] = v[f];
-        // the conic (A, B, C) back from the staged coefficients (exact)
-        if (lane == 0) rinfo[nslot] = make_float4(-2.f * a.z, -a.w, -2.f * bb.x, __uint_as_float(sp[j].id));
+        // the conic (A, B, C) back from the staged base-2 coefficients
+        if (lane == 0)
+          rinfo[nslot] = make_float4(-2.f * LN2 * a.z, -LN2 * a.w, -2.f * LN2 * bb.x, __uint_as_float(sp[j].id));
         if (++nslot == RB_SLOTS) {
           flush_partials(red, rinfo, nslot, lane, g2, V);
           nslot = 0;
