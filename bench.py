@@ -823,7 +823,7 @@ def profiled_traffic(stage, workload="street100m"):
     raster kernels' source changed since the capture."""
     if stage not in ("raster_fwd", "raster_bwd") or workload != "street100m":
         return None
-    path = os.path.join(ROOT, "profiles", "raster_adam_street100m_cache2gb.md")
+    path = os.path.join(ROOT, "profiles", "raster_street100m_cache2gb.md")
     try:
         text = open(path).read()
         sha = raster_source_sha()
