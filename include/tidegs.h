@@ -76,7 +76,9 @@ typedef struct tgs_config {
   uint32_t spare_slots;    /* extra HBM slots that receive incoming blocks while the
                               current step still uses its resident set */
   uint32_t max_batch;      /* largest camera batch J */
-  uint32_t max_width, max_height;
+  uint32_t max_width, max_height;  /* largest image; (ceil(w/16) + 1) x (ceil(h/16) + 1) <= 40,960
+                              (the tile binning's difference array in shared memory: up
+                              to 3840 x 2160 and beyond); larger is TGS_ERR_INVALID */
   uint32_t quota;          /* per-camera quota of the camera-balanced Top-C;
                               0xFFFFFFFF = floor(C / (2 J)) */
   float lambda;            /* residency mix lambda of s(k) (Sec. 3.5) */
@@ -366,7 +368,8 @@ tgs_status tgs_set_predictor(tgs_table* t, tgs_mlp* m, float threshold, uint32_t
  * ------------------------------------------------------------------------- */
 typedef struct tgs_raster tgs_raster;
 
-/* max_gaussians: largest n; max_width / max_height: largest image. */
+/* max_gaussians: largest n; max_width / max_height: largest image (the same
+ * bound as tgs_config's max_width / max_height). */
 tgs_status tgs_raster_create(uint64_t max_gaussians, uint32_t max_width, uint32_t max_height, tgs_raster** out);
 void tgs_raster_destroy(tgs_raster* r);
 

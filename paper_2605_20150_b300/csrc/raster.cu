@@ -67,6 +67,14 @@ __device__ __forceinline__ uint32_t sr_key(uint32_t seed, uint64_t gid, uint32_t
   return (uint32_t)mix64(((uint64_t)seed << 40) ^ (gid * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)step << 20));
 }
 
+// i / B for a render-list position (a shift when B is a power of two: the
+// branch is uniform)
+__device__ __forceinline__ unsigned item_of(uint64_t i, uint32_t B) {
+  const uint32_t sh = (uint32_t)__ffs(B) - 1u;
+  if (B == 1u << sh) return (unsigned)(i >> sh);
+  return (unsigned)(i / B);
+}
+
 // FP32 -> BF16: round to nearest even, or stochastically with the 16 random
 // bits r (added below the kept mantissa, then truncated; unbiased in
 // expectation).
@@ -1034,7 +1042,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_preprocess_bwd(RenderList rl, De
     const uint32_t n = *nrows;
     for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
       const uint32_t i = rows[t];
-      const unsigned item = i / B, lane = i - item * B;
+      const unsigned item = item_of(i, B), lane = i - item * B;
       pbwd_row<BF>(rl, c, ntiles, rgbv, conic_o, g2, V, grad, Vg, mode, item, lane, i, true);
     }
     return;
@@ -1059,7 +1067,7 @@ __global__ void __launch_bounds__(PP_THREADS, 2) k_preprocess_bwd_batch(RenderLi
   const uint32_t n = *nrows;
   for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
     const uint32_t i = rows[t];
-    const unsigned item = i / B, lane = i - item * B;
+    const unsigned item = item_of(i, B), lane = i - item * B;
     const uint64_t sbase = (uint64_t)rl.item_slot[item] * rl.slot_stride + lane;
     const float* p = rl.base + sbase;
     const __nv_bfloat16* q16 = sh16(rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride, B, lane);
@@ -1128,6 +1136,13 @@ __global__ void k_touched_rows(const uint8_t* __restrict__ touched, uint64_t V, 
   }
 }
 
+// sqrt(x) for Adam's denominator from the fast reciprocal square root
+// (relative error about 1e-7; x >= 0)
+__device__ __forceinline__ float adam_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// The parameter's 16 rounding bits: a second finaliser of the field's 32-bit
+// draw h (whose two halves round m and v).
+__device__ __forceinline__ uint32_t param_draw(uint32_t h) { return fmix32(h ^ 0x27D4EB2Fu); }
+
 constexpr int ADAM_FG = 4;  // fields per thread
 constexpr int ADAM_GROUPS = (D + ADAM_FG - 1) / ADAM_FG;
 
@@ -1171,7 +1186,7 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
         m[o] = mn;
         v[o] = vn;
-        p[o] = pf[q] - lrs.g[lr_group(f)] * __fdividef(mn * ic1, sqrtf(vn * ic2) + eps);
+        p[o] = pf[q] - lrs.g[lr_group(f)] * __fdividef(mn * ic1, adam_sqrt(vn * ic2) + eps);
       }
     }
   } else {
@@ -1199,14 +1214,14 @@ __device__ __forceinline__ void adam_row(const RenderList& rl, const float* __re
         const uint64_t o = (uint64_t)f * B;
         const float mn = b1 * mf[q] + (1.f - b1) * gf[q];
         const float vn = b2 * vf[q] + (1.f - b2) * gf[q] * gf[q];
-        const float upd = lrs.g[lr_group(f)] * __fdividef(mn * ic1, sqrtf(vn * ic2) + eps);
+        const float upd = lrs.g[lr_group(f)] * __fdividef(mn * ic1, adam_sqrt(vn * ic2) + eps);
         const uint32_t h = sr ? fmix32(key + (uint32_t)f * 0x9E3779B9u) : 0u;
         m[o] = to_bf16(mn, sr, h);
         v[o] = to_bf16(vn, sr, h >> 16);
         if (f < F_BF16)
           p[o] = pf[q] - upd;
         else
-          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, sr ? fmix32(h ^ 0x27D4EB2Fu) : 0u);
+          q16[(uint64_t)(f - F_BF16) * B] = to_bf16(pf[q] - upd, sr, param_draw(h));
       }
     }
   }
@@ -1252,10 +1267,10 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
         float2 mn, vn, pn;
         mn.x = b1 * mf[q].x + (1.f - b1) * gf[q].x;
         vn.x = b2 * vf[q].x + (1.f - b2) * gf[q].x * gf[q].x;
-        pn.x = pf[q].x - lr * __fdividef(mn.x * ic1, sqrtf(vn.x * ic2) + eps);
+        pn.x = pf[q].x - lr * __fdividef(mn.x * ic1, adam_sqrt(vn.x * ic2) + eps);
         mn.y = b1 * mf[q].y + (1.f - b1) * gf[q].y;
         vn.y = b2 * vf[q].y + (1.f - b2) * gf[q].y * gf[q].y;
-        pn.y = pf[q].y - lr * __fdividef(mn.y * ic1, sqrtf(vn.y * ic2) + eps);
+        pn.y = pf[q].y - lr * __fdividef(mn.y * ic1, adam_sqrt(vn.y * ic2) + eps);
         if (!t0) { mn.x = mf[q].x; vn.x = vf[q].x; pn.x = pf[q].x; }
         if (!t1) { mn.y = mf[q].y; vn.y = vf[q].y; pn.y = pf[q].y; }
         *reinterpret_cast<float2*>(m + o) = mn;
@@ -1303,8 +1318,8 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
         const float mnx = b1 * mo.x + (1.f - b1) * gf[q].x, mny = b1 * mo.y + (1.f - b1) * gf[q].y;
         const float vnx = b2 * vo.x + (1.f - b2) * gf[q].x * gf[q].x;
         const float vny = b2 * vo.y + (1.f - b2) * gf[q].y * gf[q].y;
-        const float ux = lr * __fdividef(mnx * ic1, sqrtf(vnx * ic2) + eps);
-        const float uy = lr * __fdividef(mny * ic1, sqrtf(vny * ic2) + eps);
+        const float ux = lr * __fdividef(mnx * ic1, adam_sqrt(vnx * ic2) + eps);
+        const float uy = lr * __fdividef(mny * ic1, adam_sqrt(vny * ic2) + eps);
         const uint32_t h0 = sr ? fmix32(key0 + (uint32_t)f * 0x9E3779B9u) : 0u;
         const uint32_t h1 = sr ? fmix32(key1 + (uint32_t)f * 0x9E3779B9u) : 0u;
         __nv_bfloat162 mw, vw;
@@ -1321,8 +1336,8 @@ __device__ __forceinline__ void adam_pair(const RenderList& rl, const float* __r
           *reinterpret_cast<float2*>(p + (uint64_t)f * B) = pn;
         } else {
           __nv_bfloat162 pw;
-          pw.x = t0 ? to_bf16(po.x - ux, sr, sr ? fmix32(h0 ^ 0x27D4EB2Fu) : 0u) : p16[q].x;
-          pw.y = t1 ? to_bf16(po.y - uy, sr, sr ? fmix32(h1 ^ 0x27D4EB2Fu) : 0u) : p16[q].y;
+          pw.x = t0 ? to_bf16(po.x - ux, sr, param_draw(h0)) : p16[q].x;
+          pw.y = t1 ? to_bf16(po.y - uy, sr, param_draw(h1)) : p16[q].y;
           q16[(uint64_t)(f - F_BF16) * (B / 2)] = pw;
         }
       }
@@ -1347,7 +1362,7 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_adam_pairs(RenderList rl, con
   for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
     const uint32_t e = prows[t];
     const uint32_t i = e & 0x3FFFFFFFu, mask = e >> 30;
-    const unsigned item = i / B, lane = i - item * B;
+    const unsigned item = item_of(i, B), lane = i - item * B;
     adam_pair<BF>(rl, grad, bias, block_step, V, lrs, b1, b2, eps, item, lane, i, mask, f0);
   }
 }
@@ -1370,7 +1385,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_adam(RenderList rl, const float*
   const int f0 = blockIdx.y * ADAM_FG;
   for (uint32_t t = blockIdx.x * PP_THREADS + threadIdx.x; t < n; t += gridDim.x * PP_THREADS) {
     const uint32_t i = rows[t];
-    const unsigned item = i / B, lane = i - item * B;
+    const unsigned item = item_of(i, B), lane = i - item * B;
     adam_row<BF>(rl, grad, bias, block_step, V, lrs, b1, b2, eps, item, lane, i, f0);
   }
 }
