@@ -180,3 +180,56 @@ def test_loss_values(orc):
     assert abs(l2 - ((a - b) ** 2).mean()) < 1e-15
     np.testing.assert_allclose(g1, np.sign(a - b) / a.size)
     np.testing.assert_allclose(g2, 2 * (a - b) / a.size)
+
+
+def _record(orc, u, v, depth, conic, opac, rgb=(0.5, 0.5, 0.5)):
+    s = np.zeros(orc.NS)
+    s[orc.U], s[orc.V], s[orc.DEPTH] = u, v, depth
+    s[orc.CA], s[orc.CB], s[orc.CC] = conic
+    s[orc.OPAC] = opac
+    s[orc.R:orc.B + 1] = rgb
+    s[orc.RADIUS] = 16
+    s[orc.X0], s[orc.Y0], s[orc.X1], s[orc.Y1] = 0, 0, 1, 1
+    s[orc.VISIBLE] = 1
+    return s
+
+
+def _composite(orc, S, W=16, H=16):
+    _, vals, ranges = orc.bin_sort(S, W, H)
+    return orc.composite_fwd(S, W, H, vals, ranges)
+
+
+def test_slack_alpha_threshold_window_grows_with_power(orc):
+    """An entry whose alpha lies within the FP32 error of the 1/255 skip gets
+    slack; the window is about 1e-5 |power| relative (the power is a quadratic
+    form of FP32 values), wider than tol_a: at |power| = 4.9 an alpha 2e-5
+    above the threshold is borderline, one 1e-3 above is not."""
+    o, px = 0.5, 10
+    for delta, borderline in ((2e-5, True), (1e-3, False)):
+        power = math.log((1.0 + delta) / (255.0 * o))
+        a = -2.0 * power / (px * px)
+        S = np.stack([_record(orc, 0.0, 0.0, 1.0, (a, 0.0, a), o)])
+        img, T, nl, sl = _composite(orc, S)
+        assert (sl[0, px] > 0) == borderline, (delta, sl[0, px])
+        # the pixel's result includes the entry either way (alpha >= 1/255)
+        assert abs(T[0, px] - (1.0 - o * math.exp(power))) < 1e-12
+        # pixels one step nearer or farther are far from the threshold
+        assert sl[0, px - 1] == 0 and sl[0, px + 1] == 0
+
+
+def test_slack_stop_window_follows_the_transmittance_product(orc):
+    """Three entries at the pixel centre (alpha = opacity): 0.9, 0.99
+    (clamped) and 0.9 - 0.1 delta, so the third leaves T' = 1e-4 (1 + delta).
+    The FP32 product of the factors carries a relative error of about
+    sum alpha / (1 - alpha) times the alphas' errors, ~1e-4 here: delta = 5e-5
+    is a borderline stop and gets slack of at least the transmittance left;
+    delta = 1e-2 is not."""
+    for delta, borderline in ((5e-5, True), (1e-2, False)):
+        S = np.stack([_record(orc, 0.0, 0.0, 1.0, (1.0, 0.0, 1.0), 0.9),
+                      _record(orc, 0.0, 0.0, 2.0, (1.0, 0.0, 1.0), 0.995),
+                      _record(orc, 0.0, 0.0, 3.0, (1.0, 0.0, 1.0), 0.9 - 0.1 * delta)])
+        img, T, nl, sl = _composite(orc, S)
+        assert (sl[0, 0] > 0) == borderline, (delta, sl[0, 0])
+        assert nl[0, 0] == 3  # T' >= 1e-4: the third entry is included
+        if borderline:
+            assert sl[0, 0] >= 2 * 1e-3 * 0.5  # 2 T max(rgb, bg) before the third entry
