@@ -793,9 +793,12 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       const float4 a = sp[j].a;
       const float4 bb = sp[j].b;
       const float cb = sp[j].c;
-      // v: sums over the thread's pixels of dpw dx, dpw dy, dpw dx^2, dpw dx dy,
-      // dpw dy^2 (dpw = dL/dpower; the conic and constant factors are applied
-      // after the reduction), dL/dopacity-activation, dL/d(r, g, b)
+      // sums over the thread's pixels (one column: dx is shared) of dpw,
+      // dpw dy and dpw dy^2 (dpw = dL/dpower), from which the five geometric
+      // sums dpw dx, dpw dy, dpw dx^2, dpw dx dy, dpw dy^2 follow (the conic
+      // and constant factors are applied after the reduction); v: the
+      // dL/dopacity-activation and dL/d(r, g, b) sums
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
       const float dx = __fsub_rn(fpx, a.x);
@@ -805,7 +808,6 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
       for (int k = 0; k < R_PPT; ++k) {
         const float dy = __fsub_rn((float)(q.py0 + k), a.y);
         const float dyy = __fmul_rn(dy, dy);
-        const float dxy = __fmul_rn(dx, dy);
         const float power = splat_power(a2dx, a.w, bb.x, dx, dy, dyy);
         float G;
         const float alpha = splat_alpha2(bb.y, power, G);
@@ -826,13 +828,16 @@ __global__ void __launch_bounds__(R_THREADS) k_raster_bwd(const uint2* __restric
         const float dsel = (ok && __fmul_rn(bb.y, G) <= ALPHA_MAX) ? dal : 0.f;
         v[5] += G * dsel;
         const float dpw = al * dsel;
-        v[0] += dpw * dx;
-        v[1] += dpw * dy;
-        v[2] += dpw * dxx;
-        v[3] += dpw * dxy;
-        v[4] += dpw * dyy;
+        s0 += dpw;
+        s1 += dpw * dy;
+        s2 += dpw * dyy;
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
+        v[0] = dx * s0;
+        v[1] = s1;
+        v[2] = dxx * s0;
+        v[3] = dx * s1;
+        v[4] = s2;
 #pragma unroll
         for (int f = 0; f < 9; ++f) red[9 * nslot + f][lane] = v[f];
         // the conic (A, B, C) back from the staged base-2 coefficients
