@@ -1436,36 +1436,123 @@ __device__ __forceinline__ float block_reduce(float v, float* sm, bool is_max, b
   return r;
 }
 
-__global__ void __launch_bounds__(256) k_bounds(RenderList rl, const uint32_t* __restrict__ only,
-                                               float4* __restrict__ spheres, const uint32_t* __restrict__ abort_flag) {
-  __shared__ float sm[8];
+// Bounds refresh: one CTA per touched block.  Each thread loads the means of
+// its BD_EPT rows of a chunk in one batch (every load of the chunk in flight
+// at once) and then their log-scales; the centre is the midpoint of the box
+// of the means and the radius the largest |mean - centre| + 3 exp(max
+// log-scale).  A block longer than one chunk reloads its rows for the radius.
+constexpr int BD_THREADS = 512;
+constexpr int BD_EPT = 8;
+constexpr uint32_t BD_CHUNK = (uint32_t)BD_THREADS * BD_EPT;
+constexpr int BD_WARPS = BD_THREADS / 32;
+
+__device__ __forceinline__ bool bounds_row(uint32_t c0, int e, uint32_t cnt, uint32_t& l) {
+  l = c0 + (uint32_t)(e * BD_THREADS) + threadIdx.x;
+  return l < cnt;
+}
+__device__ __forceinline__ void bounds_means(const float* __restrict__ p, uint32_t B, uint32_t cnt, uint32_t c0,
+                                             float (&pos)[BD_EPT][3]) {
+#pragma unroll
+  for (int e = 0; e < BD_EPT; ++e) {
+    uint32_t l;
+    if (bounds_row(c0, e, cnt, l))
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pos[e][a] = p[(uint64_t)a * B + l];
+  }
+}
+__device__ __forceinline__ void bounds_scales(const float* __restrict__ p, uint32_t B, uint32_t cnt, uint32_t c0,
+                                              float (&ls)[BD_EPT]) {
+#pragma unroll
+  for (int e = 0; e < BD_EPT; ++e) {
+    uint32_t l;
+    if (bounds_row(c0, e, cnt, l))
+      ls[e] = fmaxf(fmaxf(p[(uint64_t)3 * B + l], p[(uint64_t)4 * B + l]), p[(uint64_t)5 * B + l]);
+  }
+}
+__device__ __forceinline__ float bounds_reach(const float (&q)[3], float ls, const float (&c)[3]) {
+  const float dx = q[0] - c[0], dy = q[1] - c[1], dz = q[2] - c[2];
+  return sqrtf(dx * dx + dy * dy + dz * dz) + 3.f * expf(ls);
+}
+
+__global__ void __launch_bounds__(BD_THREADS, 2) k_bounds(RenderList rl, const uint32_t* __restrict__ only,
+                                                         float4* __restrict__ spheres,
+                                                         const uint32_t* __restrict__ abort_flag) {
+  __shared__ float s_red[6][BD_WARPS];
+  __shared__ float s_c[3];
   const unsigned item = blockIdx.x;
   if ((only && !only[item]) || (abort_flag && *abort_flag)) return;
   const uint32_t B = rl.B, cnt = rl.item_count[item];
   const float* p = rl.base + (uint64_t)rl.item_slot[item] * rl.slot_stride;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x)
+  float pos[BD_EPT][3], ls[BD_EPT];
+  for (uint32_t c0 = 0; c0 < cnt; c0 += BD_CHUNK) {
+    bounds_means(p, B, cnt, c0, pos);
+#pragma unroll
+    for (int e = 0; e < BD_EPT; ++e) {
+      uint32_t l;
+      if (bounds_row(c0, e, cnt, l))
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          mn[a] = fminf(mn[a], pos[e][a]);
+          mx[a] = fmaxf(mx[a], pos[e][a]);
+        }
+    }
+  }
+  const bool one_chunk = cnt <= BD_CHUNK;
+  if (one_chunk) bounds_scales(p, B, cnt, 0, ls);  // in flight during the reduction
+  // the six extrema of the box: warps, then warp 0 over the warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      float v = p[(uint64_t)a * B + l];
-      mn[a] = fminf(mn[a], v);
-      mx[a] = fmaxf(mx[a], v);
+      mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+      mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
     }
-  float c[3];
+  if (lane == 0)
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float lo = block_reduce(mn[a], sm, false, true);
-    float hi = block_reduce(mx[a], sm, true, false);
-    c[a] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    for (int a = 0; a < 3; ++a) {
+      s_red[a][w] = mn[a];
+      s_red[3 + a][w] = mx[a];
+    }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float lo = lane < BD_WARPS ? s_red[a][lane] : INFINITY;
+      float hi = lane < BD_WARPS ? s_red[3 + a][lane] : -INFINITY;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) s_c[a] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    }
   }
+  __syncthreads();
+  const float c[3] = {s_c[0], s_c[1], s_c[2]};
   float r = 0.f;
-  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
-    float dx = p[l] - c[0], dy = p[(uint64_t)B + l] - c[1], dz = p[(uint64_t)2 * B + l] - c[2];
-    float ls = fmaxf(fmaxf(p[(uint64_t)3 * B + l], p[(uint64_t)4 * B + l]), p[(uint64_t)5 * B + l]);
-    r = fmaxf(r, sqrtf(dx * dx + dy * dy + dz * dz) + 3.f * expf(ls));
+  for (uint32_t c0 = 0; c0 < cnt; c0 += BD_CHUNK) {
+    if (!one_chunk) {
+      bounds_means(p, B, cnt, c0, pos);
+      bounds_scales(p, B, cnt, c0, ls);
+    }
+#pragma unroll
+    for (int e = 0; e < BD_EPT; ++e) {
+      uint32_t l;
+      if (bounds_row(c0, e, cnt, l)) r = fmaxf(r, bounds_reach(pos[e], ls[e], c));
+    }
   }
-  r = block_reduce(r, sm, true, false);
-  if (threadIdx.x == 0) spheres[rl.item_block[item]] = make_float4(c[0], c[1], c[2], r);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if (lane == 0) s_red[0][w] = r;  // warp 0 read the box extrema before the barrier above
+  __syncthreads();
+  if (w == 0) {
+    r = lane < BD_WARPS ? s_red[0][lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) spheres[rl.item_block[item]] = make_float4(c[0], c[1], c[2], r);
+  }
 }
 
 __global__ void k_loss(const float* __restrict__ img, const float* __restrict__ tgt, uint64_t n, int kind,
@@ -1912,7 +1999,7 @@ void mark_touched_blocks(const RenderList& rl, const uint32_t* item_touched, uin
 void block_bounds(const RenderList& rl, const uint32_t* only_flag, float4* spheres, cudaStream_t s,
                   const uint32_t* abort_flag) {
   if (rl.n_items == 0) return;
-  k_bounds<<<rl.n_items, 256, 0, s>>>(rl, only_flag, spheres, abort_flag);
+  k_bounds<<<rl.n_items, BD_THREADS, 0, s>>>(rl, only_flag, spheres, abort_flag);
   TGS_LAUNCHED();
 }
 

@@ -4,7 +4,7 @@
 // normalised), zero padding outside the image, C1 = 0.01^2, C2 = 0.03^2,
 // averaged over every pixel and channel of the batch.
 //
-// Forward (k_ssim_fwd): a CTA takes a 32 x 64 tile of one channel of one
+// Forward (k_ssim_fwd): a CTA takes a 32 x 48 tile of one channel of one
 // image, stages x and y with a 5-pixel halo in shared memory, filters four
 // moment maps (x, y, x^2 + y^2, xy: the two second moments enter S only
 // through their sum, in B2) along rows and then columns (each thread a run of
@@ -30,14 +30,15 @@ namespace {
 constexpr int SS_R = 5;
 constexpr int SS_K = 2 * SS_R + 1;
 constexpr int SS_TW = 32;               // output tile width
-constexpr int SS_TH = 64;               // output tile height
+constexpr int SS_TH = 48;               // output tile height
 constexpr int SS_HW = SS_TW + 2 * SS_R;  // 42: staged width with the halo
-constexpr int SS_HH = SS_TH + 2 * SS_R;  // 74: staged height with the halo
+constexpr int SS_HH = SS_TH + 2 * SS_R;  // 58: staged height with the halo
 constexpr int SS_P = SS_HW + 1;         // padded row of a staged map
 constexpr int SS_Q = SS_TW + 1;         // padded row of a row-filtered map
 constexpr int SS_RUN = 8;               // outputs per thread along a pass
 constexpr int SS_RW = SS_TW / SS_RUN;   // row runs per staged row
-constexpr int SS_THREADS = 320;         // >= SS_HH * SS_RW (row pass) and SS_TW * SS_TH / SS_RUN (column pass)
+constexpr int SS_THREADS = 256;         // >= SS_HH * SS_RW (row pass) and SS_TW * SS_TH / SS_RUN (column pass)
+constexpr int SS_CTAS = 4;              // per SM: 64 registers a thread, about 53 KB of shared memory a CTA
 constexpr float SS_C1 = 0.01f * 0.01f, SS_C2 = 0.03f * 0.03f;
 static_assert(SS_THREADS >= SS_HH * SS_RW && SS_THREADS >= SS_TW * SS_TH / SS_RUN, "one run per thread and pass");
 
@@ -59,17 +60,33 @@ Window gaussian_window() {
 
 // Stages NM maps of one channel with the halo, zero outside the image, into
 // t[m][SS_HH][SS_P].  Interleaved-RGB maps (stride 3, channel c) or planar.
+// A thread's SS_ST elements are loaded in one batch (every load in flight at
+// once) and then stored.
+constexpr int SS_NST = SS_HH * SS_HW;
+constexpr int SS_ST = (SS_NST + SS_THREADS - 1) / SS_THREADS;
 template <int NM, bool RGB>
 __device__ __forceinline__ void stage(const float* const* maps, int W, int H, int c, uint64_t plane, int x0,
                                       int y0, float* t) {
-  for (int e = threadIdx.x; e < SS_HH * SS_HW; e += SS_THREADS) {
+  float v[SS_ST][NM];
+#pragma unroll
+  for (int i = 0; i < SS_ST; ++i) {
+    const int e = threadIdx.x + i * SS_THREADS;
     const int ly = e / SS_HW, lx = e - ly * SS_HW;
     const int gx = x0 + lx - SS_R, gy = y0 + ly - SS_R;
-    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const bool in = e < SS_NST && gx >= 0 && gx < W && gy >= 0 && gy < H;
     const uint64_t p = (uint64_t)gy * W + gx;
     const uint64_t o = RGB ? plane * 3 + p * 3 + c : plane + p;
 #pragma unroll
-    for (int m = 0; m < NM; ++m) t[(m * SS_HH + ly) * SS_P + lx] = in ? maps[m][o] : 0.f;
+    for (int m = 0; m < NM; ++m) v[i][m] = in ? maps[m][o] : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < SS_ST; ++i) {
+    const int e = threadIdx.x + i * SS_THREADS;
+    if (e < SS_NST) {
+      const int ly = e / SS_HW, lx = e - ly * SS_HW;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) t[(m * SS_HH + ly) * SS_P + lx] = v[i][m];
+    }
   }
 }
 
@@ -137,7 +154,7 @@ __device__ __forceinline__ bool col_pass(const Window& win, const float* h, int&
   return true;
 }
 
-__global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y,
+__global__ void __launch_bounds__(SS_THREADS, SS_CTAS) k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y,
                                                         int W, int H, Window win, float lam,
                                                         float* __restrict__ dm, float* __restrict__ dxx,
                                                         float* __restrict__ dxy, float* __restrict__ loss_sum) {
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(const float* __restrict
   }
 }
 
-__global__ void __launch_bounds__(SS_THREADS) k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y,
+__global__ void __launch_bounds__(SS_THREADS, SS_CTAS) k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y,
                                                         int W, int H, Window win, float lam, float inv_n,
                                                         const float* __restrict__ dm,
                                                         const float* __restrict__ dxx,
