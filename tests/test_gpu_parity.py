@@ -28,10 +28,13 @@ def _setup(orc, tgs, loss=1, n=20000, block_size=1250, **cfg):
     return c, perm, Pm, cams, targets, table
 
 
-def test_create_block_order_and_spheres(orc, tgs):
-    c, perm, Pm, cams, targets, table = _setup(orc, tgs)
+@pytest.mark.parametrize("B", [1250, 9000])
+def test_create_block_order_and_spheres(orc, tgs, B):
+    # B = 9000: blocks longer than one chunk of the bounds kernel (4,096 rows),
+    # the last one ragged (2,000 rows)
+    c, perm, Pm, cams, targets, table = _setup(orc, tgs, block_size=B)
     assert np.array_equal(table.block_order(), perm)
-    sph_o = orc.block_spheres(Pm.astype(np.float64), 1250)
+    sph_o = orc.block_spheres(Pm.astype(np.float64), B)
     sph_g = table.spheres()
     np.testing.assert_allclose(sph_g, sph_o, rtol=2e-6, atol=2e-6)
     table.close()
