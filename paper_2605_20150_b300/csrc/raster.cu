@@ -5,10 +5,13 @@
 //  k_preprocess      one thread per Gaussian: coalesced field-major loads from
 //                    the block slot, EWA projection, degree-3 SH colour, tile
 //                    rect; exact FP32 key path for centre and depth.
-//  visible compaction + stable depth sort of the visible Gaussians + pair
-//  emission in depth order + stable tile sort (the tile/depth order of the
-//  pairs equals a stable sort of (tile << 32 | depth bits) keys emitted in id
-//  order, with far fewer radix passes over the pairs).
+//  binning (tiles.cu): per-tile pair counts from the tile rects, pairs
+//  placed in their tile's range and sorted per tile on (depth bits,
+//  render-list position), the order of one stable sort of (tile << 32 |
+//  depth bits) keys emitted in render-list order.  The fixed-capacity render
+//  (render_forward_fixed) reaches the same order by visible compaction, a
+//  stable radix sort of the visible Gaussians by depth, pair emission in
+//  depth order and a stable radix sort of the pairs by tile.
 //  k_raster_fwd      one CTA per 16x16 tile (8 warps of 8 x 4 pixels, one
 //                    pixel per thread), 32 splats per warp staged in shared
 //                    memory, front-to-back blending with the 0.99 clamp,
