@@ -838,6 +838,41 @@ def profiled_traffic(stage, workload="street100m"):
     return vals.get("t") if vals.get("sha") == sha else None
 
 
+# Algorithmic HBM bytes per touched Gaussian of the HBM-bound stages whose
+# traffic the step's counts fix: Adam reads and writes the parameters and both
+# moments (FP32 record 3 x 236 B + the 236 B gradient read, plus the block's
+# step counter and slot; BF16 record 146 + 2 x 118 + 236 + ...), the backward
+# preprocess reads the parameters and the nine 2D gradients and writes the
+# 59-column gradient.
+HBM_BYTES = {"adam": {False: 1652.0, True: 1000.0},
+             "preprocess_bwd": {False: 236.0 + 36.0 + 236.0, True: 146.0 + 36.0 + 236.0}}
+
+
+def hbm_stages(res, workload="street100m"):
+    """Achieved GB/s and fraction of the measured HBM peak of the HBM-bound
+    stages, from their CUDA-event times and the touched Gaussians of a
+    batch-1 step (the visible count of its single camera); None for batches
+    of several cameras, whose touched set is the union over the cameras."""
+    if workload == "city":
+        return None
+    hbm, src = measured_peaks()
+    touched = float(res["stats"]["last_visible"])
+    steps = res.get("stage_steps") or 1
+    out = {}
+    for name, per in HBM_BYTES.items():
+        if name not in res["stages"]:
+            continue
+        tot, cnt = res["stages"][name]
+        ms = tot / max(1, cnt) if cnt else tot / steps
+        if ms <= 0:
+            continue
+        b = per[bool(res.get("bf16"))] * touched
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_launch": round(ms, 4), "bytes_per_launch": b, "achieved_gbs": round(gbs, 1),
+                     "peak_gbs": hbm, "frac": round(gbs / hbm, 4), "peak_source": src}
+    return out
+
+
 def roofline(res, steps, workload="street100m"):
     """Roofline of the dominant stage.  Raster: FP32 ALU bound, achieved =
     evaluated pairs (sum of n_last over pixels) x instructions per pair / time
@@ -1162,6 +1197,7 @@ def main():
                 "h2d_bytes_per_step": res["bytes_in"], "d2h_bytes_per_step": 4},
         "gpu_launches": int(res["launches"]),
         "roofline": roofline(res, args.steps, args.workload),
+        "hbm_stages": hbm_stages(res, args.workload),
         "clocks": res["clocks"],
         "stages_ms_per_step": {k: round(v[0] / res.get("stage_steps", args.steps), 4) for k, v in res["stages"].items()},
         "visible": res["stats"]["last_visible"], "pairs": res["stats"]["last_pairs"],
