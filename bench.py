@@ -839,11 +839,11 @@ def profiled_traffic(stage, workload="street100m"):
 
 
 # Algorithmic HBM bytes per touched Gaussian of the HBM-bound stages whose
-# traffic the step's counts fix: Adam reads and writes the parameters and both
-# moments (FP32 record 3 x 236 B + the 236 B gradient read, plus the block's
-# step counter and slot; BF16 record 146 + 2 x 118 + 236 + ...), the backward
-# preprocess reads the parameters and the nine 2D gradients and writes the
-# 59-column gradient.
+# traffic the step's counts fix: Adam reads the record (parameters and both
+# moments, 708 B FP32 / 382 B BF16) and the 236 B FP32 gradient and writes the
+# record back (1652 / 1000 B); the backward preprocess reads the parameters
+# (236 / 146 B) and the nine 2D gradients (36 B) and writes the 59-column
+# gradient (236 B).
 HBM_BYTES = {"adam": {False: 1652.0, True: 1000.0},
              "preprocess_bwd": {False: 236.0 + 36.0 + 236.0, True: 146.0 + 36.0 + 236.0}}
 
