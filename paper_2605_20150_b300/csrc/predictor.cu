@@ -272,6 +272,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(const float* __res
     if (!__syncthreads_or(!ok)) continue;
     break;
   }
+  // after a wait that ran out the tensor cores may still be writing the
+  // accumulator: wait for that phase once more (bounded) before the columns
+  // are freed
+  if (__syncthreads_or(!ok)) mbar_wait(mb, parity ^ 1u);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
