@@ -1730,7 +1730,6 @@ void cam_state_grow_pairs(CamState& cs, uint64_t need, cudaStream_t s) {
   size_t sb = radix_scratch_bytes(want);
   size_t sc = scan_scratch_bytes(want);
   if (sc > sb) sb = sc;
-  if (radix_dev_scratch_bytes(want) > sb) sb = radix_dev_scratch_bytes(want);
   if (sb > cs.scratch_bytes) {
     if (s) TGS_CUDA(cudaStreamSynchronize(s));
     if (cs.scratch) TGS_CUDA(cudaFree(cs.scratch));

@@ -1,6 +1,7 @@
-// Device-wide exclusive scan and stable LSD radix sort, used for the depth
-// sort of the visible Gaussians and the stable regrouping of their
-// (tile, Gaussian) pairs by tile in Level-2 rendering.
+// Device-wide exclusive scan and stable LSD radix sort: the Morton order of a
+// new table, the scans of Algorithm 1 and of the predictor's candidate
+// blocks, and, in the fixed-capacity render, the depth sort of the visible
+// Gaussians and the stable regrouping of their (tile, Gaussian) pairs by tile.
 //
 // A radix pass = histogram kernel + scan of the digit-major count table +
 // scatter kernel.  The scatter ranks keys stably inside a 4096-key tile with
@@ -269,111 +270,6 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
 }
 
 
-// ---- device-count variants: the element count lives in device memory, so a
-// sort or scan can follow the kernel that produced its input without a host
-// round trip.  Grids are fixed by a host-known capacity.
-
-__device__ __forceinline__ uint64_t dev_count(const uint32_t* n_dev, uint64_t cap) {
-  uint64_t n = *n_dev;
-  return n < cap ? n : cap;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce_dev(const uint32_t* __restrict__ in,
-                                                                 const uint32_t* __restrict__ n_dev, uint64_t cap,
-                                                                 uint32_t* __restrict__ partial) {
-  const uint64_t n = dev_count(n_dev, cap);
-  __shared__ uint32_t sw[SCAN_THREADS / 32 + 1];
-  uint64_t base = (uint64_t)blockIdx.x * SCAN_CHUNK;
-  uint32_t s = 0;
-  if (base < n) {
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-      uint64_t p = base + (uint64_t)i * SCAN_THREADS + threadIdx.x;
-      if (p < n) s += in[p];
-    }
-  }
-  uint32_t tot;
-  block_excl_scan<SCAN_THREADS>(s, sw, &tot);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply_dev(const uint32_t* __restrict__ in,
-                                                                uint32_t* __restrict__ out,
-                                                                const uint32_t* __restrict__ n_dev, uint64_t cap,
-                                                                const uint32_t* __restrict__ partial) {
-  const uint64_t n = dev_count(n_dev, cap);
-  uint64_t base = (uint64_t)blockIdx.x * SCAN_CHUNK;
-  if (base >= n) return;  // uniform per CTA
-  __shared__ uint32_t buf[SCAN_CHUNK + SCAN_CHUNK / 32];
-  __shared__ uint32_t sw[SCAN_THREADS / 32 + 1];
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int q = i * SCAN_THREADS + threadIdx.x;
-    uint64_t p = base + q;
-    buf[q + (q >> 5)] = p < n ? in[p] : 0;
-  }
-  __syncthreads();
-  uint32_t v[SCAN_ITEMS];
-  uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int q = threadIdx.x * SCAN_ITEMS + i;
-    v[i] = buf[q + (q >> 5)];
-    s += v[i];
-  }
-  uint32_t e = block_excl_scan<SCAN_THREADS>(s, sw, nullptr) + partial[blockIdx.x];
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int q = threadIdx.x * SCAN_ITEMS + i;
-    buf[q + (q >> 5)] = e;
-    e += v[i];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int q = i * SCAN_THREADS + threadIdx.x;
-    uint64_t p = base + q;
-    if (p < n) out[p] = buf[q + (q >> 5)];
-  }
-}
-
-// Chunking of a device-count sort over G CTAs: CTA c owns the tiles
-// [c * per, min(T, (c + 1) * per)) of T = ceil(n / RS_TILE), so chunks are
-// contiguous and in CTA order (the stability of the pass).
-struct Chunk {
-  uint64_t n, first, last;  // elements [first, last)
-};
-__device__ __forceinline__ Chunk sort_chunk(const uint32_t* n_dev, uint64_t cap) {
-  Chunk c;
-  c.n = dev_count(n_dev, cap);
-  const uint64_t T = (c.n + RS_TILE - 1) / RS_TILE;
-  const uint64_t per = (T + gridDim.x - 1) / gridDim.x;
-  c.first = (uint64_t)blockIdx.x * per * RS_TILE;
-  c.last = c.first + per * RS_TILE;
-  if (c.last > c.n) c.last = c.n;
-  if (c.first > c.last) c.first = c.last;
-  return c;
-}
-
-__global__ void __launch_bounds__(RS_THREADS) k_rsd_hist(const uint32_t* __restrict__ keys,
-                                                        const uint32_t* __restrict__ n_dev, uint64_t cap, int shift,
-                                                        uint32_t mask, uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[RS_WARPS][RS_BINS];
-  const int w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const Chunk c = sort_chunk(n_dev, cap);
-  for (uint64_t p = c.first + threadIdx.x; p < c.last; p += RS_THREADS)
-    atomicAdd(&h[w][(keys[p] >> shift) & mask], 1u);
-  __syncthreads();
-  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < RS_WARPS; ++k) s += h[k][d];
-    counts[(uint64_t)d * gridDim.x + blockIdx.x] = s;
-  }
-}
-
 // One CTA: exclusive scan of the digit-major count table counts[d][c] in
 // place, which gives the global start of (digit d, chunk c).  Each thread
 // scans a contiguous segment (independent loads, cached lines), the segment
@@ -397,108 +293,6 @@ __global__ void __launch_bounds__(RSO_THREADS) k_rsd_offsets(uint32_t* __restric
     const uint32_t x = counts[i];
     counts[i] = run;
     run += x;
-  }
-}
-
-// Stable scatter of one chunk, tile by tile: each 4,096-key tile is ranked
-// with warp multi-split, staged in shared memory in digit order and written
-// as contiguous digit runs; the chunk's running digit offsets advance by the
-// tile's digit counts.
-__global__ void __launch_bounds__(RS_THREADS) k_rsd_scatter(const uint32_t* __restrict__ kin,
-                                                           const uint32_t* __restrict__ vin,
-                                                           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                           const uint32_t* __restrict__ n_dev, uint64_t cap,
-                                                           int shift, uint32_t mask,
-                                                           const uint32_t* __restrict__ offs) {
-  __shared__ uint32_t cnt[RS_WARPS][RS_BINS];
-  __shared__ uint32_t dstart[RS_BINS];
-  __shared__ uint32_t goff[RS_BINS];
-  __shared__ uint32_t sw[RS_THREADS / 32 + 1];
-  __shared__ uint32_t sk[RS_TILE];
-  __shared__ uint32_t sv[RS_TILE];
-  const Chunk ch = sort_chunk(n_dev, cap);
-  if (ch.first >= ch.last) return;  // uniform per CTA
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) goff[d] = offs[(uint64_t)d * gridDim.x + blockIdx.x];
-  for (uint64_t t0 = ch.first; t0 < ch.last; t0 += RS_TILE) {
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&cnt[0][0])[i] = 0;
-    __syncthreads();
-    // warp w ranks the run [w*512, w*512+512) of the tile in input order
-    const uint64_t base = t0 + (uint64_t)w * (32 * RS_ITEMS);
-    uint32_t key[RS_ITEMS], val[RS_ITEMS], rk[RS_ITEMS];
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-      uint64_t p = base + (uint64_t)j * 32 + lane;
-      bool valid = p < ch.last;
-      key[j] = valid ? kin[p] : 0u;
-      val[j] = valid ? vin[p] : 0u;
-      uint32_t d = valid ? ((key[j] >> shift) & mask) : (uint32_t)RS_BINS;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (lane == leader && valid) {
-        old = cnt[w][d];
-        cnt[w][d] = old + __popc(peers);
-      }
-      old = __shfl_sync(0xffffffffu, old, leader);
-      rk[j] = old + __popc(peers & lt);
-      __syncwarp();
-    }
-    __syncthreads();
-    uint32_t tot;
-    {
-      const int d = threadIdx.x;  // RS_THREADS == RS_BINS
-      uint32_t run = 0;
-#pragma unroll
-      for (int k = 0; k < RS_WARPS; ++k) {
-        uint32_t c = cnt[k][d];
-        cnt[k][d] = run;
-        run += c;
-      }
-      tot = run;
-    }
-    uint32_t ds = block_excl_scan<RS_THREADS>(tot, sw, nullptr);
-    dstart[threadIdx.x] = ds;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-      uint64_t p = base + (uint64_t)j * 32 + lane;
-      if (p < ch.last) {
-        uint32_t d = (key[j] >> shift) & mask;
-        uint32_t pos = dstart[d] + cnt[w][d] + rk[j];
-        sk[pos] = key[j];
-        sv[pos] = val[j];
-      }
-    }
-    __syncthreads();
-    uint64_t tile_n = ch.last - t0;
-    if (tile_n > RS_TILE) tile_n = RS_TILE;
-#pragma unroll 4
-    for (int i = 0; i < RS_ITEMS; ++i) {
-      uint32_t e = i * RS_THREADS + threadIdx.x;
-      if (e < tile_n) {
-        uint32_t k = sk[e];
-        uint32_t d = (k >> shift) & mask;
-        uint32_t g = goff[d] + (e - dstart[d]);
-        kout[g] = k;
-        vout[g] = sv[e];
-      }
-    }
-    __syncthreads();
-    goff[threadIdx.x] += tot;  // RS_THREADS == RS_BINS
-    // the next tile's zeroing of cnt follows this tile's reads of cnt/dstart
-    __syncthreads();
-  }
-}
-
-__global__ void k_copy_pairs_dev(const uint32_t* __restrict__ ks, const uint32_t* __restrict__ vs,
-                                 uint32_t* __restrict__ kd, uint32_t* __restrict__ vd,
-                                 const uint32_t* __restrict__ n_dev, uint64_t cap) {
-  const uint64_t n = dev_count(n_dev, cap);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    kd[i] = ks[i];
-    vd[i] = vs[i];
   }
 }
 
@@ -562,73 +356,6 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
   if (passes & 1) {
     TGS_CUDA(cudaMemcpyAsync(keys, ki, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     TGS_CUDA(cudaMemcpyAsync(vals, vi, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-  }
-}
-
-static uint32_t rsd_ctas(uint64_t cap) {
-  uint64_t t = div_up(cap > 0 ? cap : 1, RS_TILE);
-  return (uint32_t)(t < 2 * NSM ? t : 2 * NSM);
-}
-
-size_t radix_dev_scratch_bytes(uint64_t cap) {
-  const uint64_t e = (uint64_t)rsd_ctas(cap) * RS_BINS;
-  return (size_t)e * sizeof(uint32_t) + scan_scratch_bytes(e) + 256;
-}
-
-size_t scan_dev_scratch_bytes(uint64_t cap) { return scan_scratch_bytes(cap); }
-
-void exclusive_scan_u32_dev(const uint32_t* in, uint32_t* out, uint32_t* total_dev, const uint32_t* n_dev,
-                            uint64_t cap, void* scratch, cudaStream_t s) {
-  if (cap == 0) {
-    if (total_dev) TGS_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s));
-    return;
-  }
-  uint32_t nc = div_up(cap, SCAN_CHUNK);
-  uint32_t* partial = (uint32_t*)scratch;
-  k_scan_reduce_dev<<<nc, SCAN_THREADS, 0, s>>>(in, n_dev, cap, partial);
-  TGS_LAUNCHED();
-  k_scan_partials<<<1, 1024, 0, s>>>(partial, nc, total_dev);
-  TGS_LAUNCHED();
-  k_scan_apply_dev<<<nc, SCAN_THREADS, 0, s>>>(in, out, n_dev, cap, partial);
-  TGS_LAUNCHED();
-}
-
-void radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                          const uint32_t* n_dev, uint64_t cap, int bits, void* scratch, cudaStream_t s,
-                          uint64_t n_hint) {
-  if (cap <= 1 || bits <= 0) return;
-  // chunks: one tile each for the expected count (any count sorts correctly)
-  uint32_t G = rsd_ctas(cap);
-  if (n_hint > 0) {
-    const uint64_t want = div_up(n_hint + n_hint / 4, RS_TILE);
-    if (want < G) G = (uint32_t)(want > 0 ? want : 1);
-  }
-  uint32_t* counts = (uint32_t*)scratch;
-  void* scan_scr = (void*)(counts + (size_t)rsd_ctas(cap) * RS_BINS);
-  const uint64_t E = (uint64_t)G * RS_BINS;
-  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
-  int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
-    int nb = bits - shift < 8 ? bits - shift : 8;
-    uint32_t mask = (1u << nb) - 1u;
-    k_rsd_hist<<<G, RS_THREADS, 0, s>>>(ki, n_dev, cap, shift, mask, counts);
-    TGS_LAUNCHED();
-    if (E <= RSO_MAX) {
-      k_rsd_offsets<<<1, RSO_THREADS, 0, s>>>(counts, G);
-      TGS_LAUNCHED();
-    } else {
-      exclusive_scan_u32(counts, counts, nullptr, E, scan_scr, s);
-    }
-    k_rsd_scatter<<<G, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, cap, shift, mask, counts);
-    TGS_LAUNCHED();
-    uint32_t* t;
-    t = ki; ki = ko; ko = t;
-    t = vi; vi = vo; vo = t;
-    ++passes;
-  }
-  if (passes & 1) {
-    k_copy_pairs_dev<<<G, 256, 0, s>>>(ki, vi, keys, vals, n_dev, cap);
-    TGS_LAUNCHED();
   }
 }
 

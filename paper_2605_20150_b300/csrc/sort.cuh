@@ -18,17 +18,4 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total_dev, 
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint64_t n,
                       int bits, void* scratch, cudaStream_t s);
 
-// Device-count forms: the element count is read at run time from n_dev
-// (device memory, clamped to cap), so they can follow the kernel that wrote
-// it without a host round trip; cap (host) sizes the grids and scratch.
-size_t scan_dev_scratch_bytes(uint64_t cap);
-size_t radix_dev_scratch_bytes(uint64_t cap);
-void exclusive_scan_u32_dev(const uint32_t* in, uint32_t* out, uint32_t* total_dev, const uint32_t* n_dev,
-                            uint64_t cap, void* scratch, cudaStream_t s);
-// n_hint (host, 0 = unknown): the expected count, which only sets how many
-// CTAs share the work.
-void radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                          const uint32_t* n_dev, uint64_t cap, int bits, void* scratch, cudaStream_t s,
-                          uint64_t n_hint = 0);
-
 }  // namespace tgs
