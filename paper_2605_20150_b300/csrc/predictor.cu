@@ -437,18 +437,6 @@ __global__ void k_mlp_round_w2(const float* __restrict__ P, __nv_bfloat16* __res
   w2r[(uint64_t)k * MLP_H + n] = __bfloat162float(b);
 }
 
-__global__ void k_mlp_threshold(const float* __restrict__ z3, uint64_t K, uint32_t mask, float zthr,
-                                uint32_t* __restrict__ bits, uint64_t words) {
-  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool vis = false;
-  if (k < K)
-#pragma unroll
-    for (int h = 0; h < MLP_OUT; ++h)
-      if ((mask >> h & 1u) && z3[k * MLP_OUT + h] > zthr) vis = true;
-  const uint32_t wd = __ballot_sync(0xffffffffu, vis);
-  if ((threadIdx.x & 31) == 0 && (k >> 5) < words) bits[k >> 5] = wd;
-}
-
 // Candidates of a prediction: blocks whose sphere comes within lim of the
 // current camera centre, lim = the distance of the frustum's far corners plus
 // how far the camera can travel over the predicted horizons; the others
@@ -687,13 +675,6 @@ void mlp_predict_near(Mlp& m, const float4* spheres, uint64_t K, const tgs_camer
   const float zthr = std::log(thr / (1.f - thr));
   TGS_CUDA(cudaMemsetAsync(bits, 0, (K + 31) / 32 * sizeof(uint32_t), s));
   k_mlp_threshold_cand<<<div_up(K, 256), 256, 0, s>>>(m.z3, m.ccount, m.cid, mask, zthr, bits);
-  TGS_LAUNCHED();
-}
-
-void mlp_threshold(const float* logits, uint64_t K, uint32_t mask, float thr, uint32_t* bits, cudaStream_t s) {
-  const float zthr = std::log(thr / (1.f - thr));
-  const uint64_t words = (K + 31) / 32;
-  k_mlp_threshold<<<div_up(words * 32, 256), 256, 0, s>>>(logits, K, mask, zthr, bits, words);
   TGS_LAUNCHED();
 }
 

@@ -70,9 +70,6 @@ void mlp_forward(Mlp& m, const float4* spheres, uint64_t K, const tgs_camera* hi
 // 0/1 floats) and one AdamW step; returns the loss (host).
 float mlp_train_step(Mlp& m, uint64_t K, const float* labels, float pos_weight, float lr, float wd,
                      bool apply, cudaStream_t s);
-// visibility bits (words of 32 blocks) of blocks whose predicted probability
-// for any horizon in `mask` exceeds thr.
-void mlp_threshold(const float* logits, uint64_t K, uint32_t mask, float thr, uint32_t* bits, cudaStream_t s);
 // Prediction over the candidate blocks only: blocks whose sphere comes within
 // reach of the ball through the far corners of the current camera's frustum
 // (hist[7]) are packed, run through the
