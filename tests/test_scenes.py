@@ -1,9 +1,12 @@
 """Pins of the seeded input generators (CPU): SplitMix64 against its published
 test vector, the counter-based streams' independence of the requested range,
 the torch streams (used for scenes of 10^8 Gaussians) against the numpy ones,
-the moments of the uniform and Box-Muller normal draws, and the street
-scene's neighbourhood rows against the same rows of the full table (the
-full-size parity tests run the oracle on such neighbourhoods)."""
+the moments of the uniform and Box-Muller normal draws, the street scene's
+neighbourhood rows against the same rows of the full table (the full-size
+parity tests run the oracle on such neighbourhoods), and the camera paths
+against their recipe (the street drive: 2 m per frame at 1.5 m on the road
+centre lines, turns at 400 m marks; the aerial lawnmower: 150 m, 45 degrees
+down, 8 m per frame, passes 400 m apart)."""
 import numpy as np
 
 import scenes
@@ -75,3 +78,48 @@ def test_street_neighbourhood_rows_equal_the_full_table():
     q = full[:, 6:10].double()
     assert torch.allclose(q.norm(dim=1), torch.ones(n, dtype=torch.float64), atol=1e-6)
     assert torch.isfinite(full).all()
+
+
+def _centre_and_view(cam):
+    R = np.asarray(cam["R"], np.float64)
+    t = np.asarray(cam["t"], np.float64)
+    return -R.T @ t, R[2]  # camera centre, viewing direction (camera +z) in the world
+
+
+def test_street_drive_follows_the_road_grid():
+    cams = scenes.street_drive_cameras(500)
+    assert len(cams) == 500
+    c = np.array([_centre_and_view(k)[0] for k in cams])
+    v = np.array([_centre_and_view(k)[1] for k in cams])
+    for k in cams[:3]:
+        R = np.asarray(k["R"])
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12) and np.linalg.det(R) > 0
+        assert (k["width"], k["height"], k["zfar"]) == (1600, 900, 200.0)
+        assert abs(2 * np.degrees(np.arctan(0.5 * k["width"] / k["fx"])) - 90.0) < 1e-9
+    assert np.allclose(c[:, 2], 1.5)                       # 1.5 m above the ground
+    assert np.allclose(np.linalg.norm(np.diff(c[:, :2], axis=0), axis=1), 2.0)  # 2 m per frame
+    assert np.all(np.abs(c[:, :2]) < 2000.0)               # inside the 4 km square
+    assert np.allclose(v[:, 2], 0.0) and np.allclose(np.linalg.norm(v, axis=1), 1.0)
+    # on a road centre line: the coordinate across the direction of travel is a
+    # multiple of 100 m
+    across = np.where(np.abs(v[:, 0]) > 0.5, c[:, 1], c[:, 0])
+    r = np.mod(across + 2000.0, 100.0)
+    assert np.all(np.minimum(r, 100.0 - r) < 1e-9)
+    # the heading changes only at 400 m (200-frame) marks, by a quarter turn or a reversal
+    turns = np.nonzero(np.any(np.abs(np.diff(v, axis=0)) > 1e-9, axis=1))[0] + 1
+    assert len(turns) >= 2 and np.all(turns % 200 == 0)
+
+
+def test_lawnmower_passes():
+    cams = scenes.lawnmower_cameras(1000)
+    c = np.array([_centre_and_view(k)[0] for k in cams])
+    v = np.array([_centre_and_view(k)[1] for k in cams])
+    assert np.allclose(c[:, 2], 150.0)
+    assert np.allclose(np.degrees(np.arcsin(-v[:, 2])), 45.0)  # pitched 45 degrees down
+    assert (cams[0]["width"], cams[0]["height"], cams[0]["zfar"]) == (1920, 1080, 600.0)
+    step = np.linalg.norm(np.diff(c[:, :2], axis=0), axis=1)
+    same_pass = np.isclose(np.diff(c[:, 1]), 0.0)
+    assert same_pass.sum() > 900 and np.allclose(step[same_pass], 8.0)  # 8 m per frame along a pass
+    ys = np.unique(np.round(c[:, 1], 6))
+    assert len(ys) >= 2 and np.allclose(np.diff(ys), 400.0)    # passes 400 m apart
+    assert np.all(np.abs(c[:, :2]) <= 2000.0)
