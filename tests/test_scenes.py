@@ -123,3 +123,19 @@ def test_lawnmower_passes():
     ys = np.unique(np.round(c[:, 1], 6))
     assert len(ys) >= 2 and np.allclose(np.diff(ys), 400.0)    # passes 400 m apart
     assert np.all(np.abs(c[:, :2]) <= 2000.0)
+
+
+def test_street_scene_recipe():
+    n = 200_000
+    full, spacing = scenes.street_scene(n, device="cpu", chunk=1 << 16)
+    p = full.double().numpy()
+    ng = n // 2
+    assert np.all(p[:ng, 2] == 0.0)                        # the ground layer
+    assert np.all(np.abs(p[:, :2]) <= 2000.0)              # inside the 4 km square
+    z = p[ng:, 2]
+    assert z.min() >= 0.0 and z.max() <= 60.0 and np.mean(z > 0) > 0.99  # facades up to 60 m
+    ls = p[:, 3:6].ravel()
+    assert abs(ls.mean() - np.log(0.5 * spacing)) < 0.005 and abs(ls.std() - 0.3) < 0.005
+    assert abs(p[:, 10].mean() - 2.0) < 0.01 and abs(p[:, 10].std() - 0.5) < 0.01
+    rest = p[:, 14:59].ravel()
+    assert abs(rest.mean()) < 1e-3 and abs(rest.std() - 0.05) < 1e-3
